@@ -1,0 +1,386 @@
+"""FP64 CPU oracle for fKK-EC and per-spectrum KK  --  TEST INFRASTRUCTURE ONLY.
+
+This module is the independent, slow, plain reference that the CUDA path is
+checked against.  Only the test-suite, the smoke check of the package entry
+point and the benchmark's CPU-baseline / reference legs may import it; the
+product path never does.  It shares no code with the CUDA library.
+
+Everything is float64 numpy.  Library primitives used as single steps: FFT
+(numpy.fft), symmetric eigendecomposition (numpy.linalg.eigh), dense and
+banded linear solves (numpy.linalg.solve, scipy.linalg.solveh_banded), and
+matrix products.
+
+Notation follows the paper (Camp, Bender & Lee, "Real-time and high-throughput
+Raman signal extraction and processing in CARS hyperspectral imaging"), with
+one deliberate renaming: here N is the number of spectra (rows) and M the
+number of channels (columns); the paper uses the opposite letters (Sec. 2.2).
+
+Readings where the paper is silent (each is also a keyword argument):
+  * ratio floor: I/I_ref is clamped below at 1e-6 before the logarithm;
+  * discrete Hilbert transform: edge-replicate pad to L = nextpow2(2M),
+    centred (floor((L-M)/2) samples on the left), multiply bin m of the DFT by
+    -i*sgn(m) with 0 at DC and at the Nyquist bin, inverse DFT, crop;
+  * no mean-centring before the SVD (Sec. 2.2 factorises A itself);
+  * eigenvector sign: the largest-magnitude component is made positive
+    (cosmetic; every use is bilinear in V or a union of argmax and argmin);
+  * detrending operator D (Eq. phi_err_USphi_b) = asymmetric least squares
+    with a second-difference penalty, lambda = 1e4 * (M/1000)^4, p = 1e-2,
+    20 iterations, weights start at 1 (chosen by the error against the known
+    truth on the synthetic workload; the paper gives no values);
+  * ridge weight (Eq. PEC_Ridge) lambda_r = 1e-3 * ||X||_F^2 / k;
+  * trendline M{} (Eq. fSEC_VT) = Savitzky-Golay of order 2 over the largest
+    odd window <= M/2, edges from the polynomial fitted to the first / last
+    full window ("interp" edges); the alternative is the plain mean;
+  * ML apply (Eq. ML_Unew): U_new S = A_new V diag(s^2 / (s^2 + lambda_ml)).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+F64 = np.float64
+
+# ---------------------------------------------------------------------------
+# Parameters
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class FitParams:
+    k: int = 20
+    pad_len: int = 0  # 0 -> nextpow2(2M)
+    pec: bool = True
+    sec: bool = True
+    als_lambda: float | None = None  # None -> 1e4 * (M/1000)^4
+    als_p: float = 1e-2
+    als_iters: int = 20
+    ridge_rel: float = 1e-3
+    sec_mode: str = "sg"  # "sg" | "mean"
+    sg_window: int = 0  # 0 -> largest odd <= M/2
+    sg_order: int = 2
+    ml_lambda: float = 0.0
+    ratio_floor: float = 1e-6
+
+
+def pad_len(n_channels: int) -> int:
+    """L = nextpow2(2M): the discrete Hilbert transform's padded length."""
+    L = 1
+    while L < 2 * n_channels:
+        L *= 2
+    return L
+
+
+def default_als_lambda(n_channels: int) -> float:
+    return 1e4 * (n_channels / 1000.0) ** 4
+
+
+def default_sg_window(n_channels: int) -> int:
+    w = n_channels // 2
+    if w % 2 == 0:
+        w -= 1
+    return max(w, 3)
+
+
+# ---------------------------------------------------------------------------
+# Eq. KCARS / Eq. K: log ratio and Hilbert transform
+# ---------------------------------------------------------------------------
+
+
+def log_ratio(i_cars, i_ref, f=None, ratio_floor: float = 1e-6) -> np.ndarray:
+    """A = f(w) * 1/2 ln(I_CARS / I_ref) row-wise (Sec. 2.2, the scaled A of
+    the heteroscedastic addendum; f = None means f = 1)."""
+    r = np.asarray(i_cars, F64) / np.asarray(i_ref, F64)
+    a = 0.5 * np.log(np.maximum(r, ratio_floor))
+    if f is not None:
+        a = a * np.asarray(f, F64)
+    return a
+
+
+def hilbert(x, L: int | None = None) -> np.ndarray:
+    """Discrete Hilbert transform of each row of x (last axis), Eq. KCARS.
+
+    Rows are edge-padded to length L (centred), transformed with the DFT,
+    bin m multiplied by -i*sgn(m) (sgn = +1 for 0 < m < L/2, -1 for m > L/2,
+    0 at m = 0 and m = L/2), inverse-transformed and cropped back.  With
+    L == M there is no padding (the periodic transform)."""
+    x = np.asarray(x, F64)
+    M = x.shape[-1]
+    if L is None:
+        L = pad_len(M)
+    if L < M:
+        raise ValueError("pad length shorter than the signal")
+    left = (L - M) // 2
+    right = L - M - left
+    pad = [(0, 0)] * (x.ndim - 1) + [(left, right)]
+    xp = np.pad(x, pad, mode="edge") if L > M else x
+    X = np.fft.fft(xp, axis=-1)
+    m = np.arange(L)
+    mult = np.zeros(L, np.complex128)
+    mult[(m > 0) & (m < L // 2)] = -1j
+    mult[m > L // 2] = 1j
+    h = np.fft.ifft(X * mult, axis=-1).real
+    return h[..., left : left + M]
+
+
+def kk_per_spectrum(i_cars, i_ref, L: int | None = None, ratio_floor: float = 1e-6):
+    """Conventional per-spectrum KK, Eq. KCARS with the surrogate of Eq. K:
+    K = sqrt(I/I_ref) exp(i H{1/2 ln(I/I_ref)}).  Returns (Re K, Im K)."""
+    a = log_ratio(i_cars, i_ref, None, ratio_floor)
+    phi = hilbert(a, L)
+    amp = np.exp(a)
+    return amp * np.cos(phi), amp * np.sin(phi)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2 (heteroscedastic addendum): noise-normalising spectrum f(w)
+# ---------------------------------------------------------------------------
+
+
+def noise_scale(mean_i, alpha: float, sigma_g: float) -> np.ndarray:
+    """f(w) from 1/f = sqrt(alpha <I> + sigma_g^2) / (2 <I>)."""
+    mean_i = np.asarray(mean_i, F64)
+    return 2.0 * mean_i / np.sqrt(alpha * mean_i + sigma_g**2)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: SVD through the Gram matrix
+# ---------------------------------------------------------------------------
+
+
+def gram(A) -> np.ndarray:
+    """G = A^T A (M x M)."""
+    A = np.asarray(A, F64)
+    return A.T @ A
+
+
+def eig_desc(G):
+    """Eigenpairs of the symmetric G sorted by descending eigenvalue, each
+    eigenvector's largest-magnitude component made positive."""
+    lam, V = np.linalg.eigh(np.asarray(G, F64))
+    order = np.argsort(lam)[::-1]
+    lam = lam[order]
+    V = V[:, order]
+    idx = np.argmax(np.abs(V), axis=0)
+    sign = np.sign(V[idx, np.arange(V.shape[1])])
+    sign[sign == 0] = 1.0
+    return lam, V * sign
+
+
+def singular_from_eig(lam) -> np.ndarray:
+    """s = sqrt(max(lambda, 0)): singular values of A from eigenvalues of A^T A."""
+    return np.sqrt(np.maximum(np.asarray(lam, F64), 0.0))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 (fPEC): sub-sampling, detrending, ridge regression
+# ---------------------------------------------------------------------------
+
+
+def select_rows(P) -> np.ndarray:
+    """q = q_max U q_min: the rows holding the largest and the smallest value
+    of each column of U (equivalently of U S, since s > 0), Eqs. q_max/q_min.
+    Ties go to the lowest row index.  Returned sorted and unique."""
+    P = np.asarray(P)
+    qmax = np.argmax(P, axis=0)
+    qmin = np.argmin(P, axis=0)
+    return np.unique(np.concatenate([qmax, qmin]))
+
+
+def als_baseline(y, lam: float, p: float, iters: int) -> np.ndarray:
+    """Asymmetric least squares baseline of one signal (the detrending operator
+    D of Eq. phi_err_USphi_b; P. Eilers' ALS as cited for PEC in Sec. 2.1).
+
+    Repeats `iters` times: solve (W + lam D2^T D2) z = W y with W = diag(w),
+    D2 the second-difference operator; then w_i = p where y_i > z_i, else 1-p.
+    Weights start at 1.  Returns z."""
+    y = np.asarray(y, F64)
+    n = y.size
+    # D2^T D2 is symmetric pentadiagonal: accumulate the outer products of the
+    # rows (1, -2, 1) of D2 into its three bands (upper banded storage).
+    d0 = np.zeros(n)
+    d1 = np.zeros(n - 1)
+    d2 = np.zeros(n - 2)
+    d0[: n - 2] += 1.0
+    d0[1 : n - 1] += 4.0
+    d0[2:] += 1.0
+    d1[: n - 2] += -2.0
+    d1[1 : n - 1] += -2.0
+    d2 += 1.0
+    w = np.ones(n)
+    z = y.copy()
+    for _ in range(iters):
+        ab = np.zeros((3, n))
+        ab[2] = lam * d0 + w
+        ab[1, 1:] = lam * d1
+        ab[0, 2:] = lam * d2
+        z = scipy.linalg.solveh_banded(ab, w * y)
+        w = np.where(y > z, p, 1.0 - p)
+    return z
+
+
+def ridge(X, Y, lam: float) -> np.ndarray:
+    """(X^T X + lam I)^-1 X^T Y, Eq. PEC_Ridge."""
+    X = np.asarray(X, F64)
+    k = X.shape[1]
+    return np.linalg.solve(X.T @ X + lam * np.eye(k), X.T @ np.asarray(Y, F64))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.4 (fSEC): trendline
+# ---------------------------------------------------------------------------
+
+
+def savgol_trend(x, window: int, order: int) -> np.ndarray:
+    """Savitzky-Golay trendline of each row: the value at j of the degree-
+    `order` least-squares polynomial over the window centred at j; within half
+    a window of either edge, the polynomial fitted to the first / last full
+    window evaluated at j."""
+    x = np.asarray(x, F64)
+    M = x.shape[-1]
+    if window > M or window % 2 == 0 or window <= order:
+        raise ValueError("bad Savitzky-Golay window")
+    h = window // 2
+    t = np.arange(-h, h + 1, dtype=F64)
+    V = np.vander(t, order + 1, increasing=True)  # window x (order+1)
+    fit = np.linalg.pinv(V)  # (order+1) x window: polynomial coefficients
+    out = np.empty_like(x)
+    rows = x.reshape(-1, M)
+    o = out.reshape(-1, M)
+    centre = fit[0]  # value of the polynomial at t = 0
+    for r in range(rows.shape[0]):
+        for j in range(h, M - h):
+            o[r, j] = centre @ rows[r, j - h : j + h + 1]
+        c_lo = fit @ rows[r, :window]
+        c_hi = fit @ rows[r, M - window :]
+        for j in range(h):
+            o[r, j] = np.polyval(c_lo[::-1], j - h)
+            o[r, M - h + j] = np.polyval(c_hi[::-1], j + 1)
+    return out
+
+
+def trend(x, mode: str, window: int, order: int) -> np.ndarray:
+    """The trendline operator M{} of Eq. fSEC_VT: Savitzky-Golay or the mean."""
+    x = np.asarray(x, F64)
+    if mode == "mean":
+        return np.repeat(x.mean(axis=-1, keepdims=True), x.shape[-1], axis=-1)
+    if mode == "sg":
+        return savgol_trend(x, window, order)
+    raise ValueError(mode)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2-2.5: fKK-EC fit and reconstruction; Sec. 2.6: ML apply
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Basis:
+    """The trained artefacts listed in Sec. 2.6 (f, S, V, Phi_PEC, V_SEC),
+    in the combined form used by the reconstruction Eq. fKKEC."""
+
+    f: np.ndarray  # (M,)
+    s: np.ndarray  # (k,) singular values
+    V: np.ndarray  # (M, k) right singular vectors of A
+    B: np.ndarray  # (k, M) V^T / f
+    H_B: np.ndarray  # (k, M) H{V^T / f}
+    phi_pec_t: np.ndarray  # (k, M) Phi_PEC^T
+    H_phi: np.ndarray  # (k, M) H{Phi_PEC^T}
+    v_sec_t: np.ndarray  # (k, M) V_SEC^T
+    c_amp: np.ndarray  # (k, M) V^T/f + H{Phi_PEC} - V_SEC^T
+    c_ph: np.ndarray  # (k, M) H{V^T/f} - Phi_PEC^T
+    i_ref: np.ndarray  # (M,)
+    params: FitParams
+    extras: dict = field(default_factory=dict)
+
+
+def reconstruct(P, c_amp, c_ph):
+    """Eq. fKKEC with U S = P: K = exp(P C_amp) exp(i P C_ph).
+    Returns (Re K, Im K)."""
+    P = np.asarray(P, F64)
+    amp = np.exp(P @ c_amp)
+    ph = P @ c_ph
+    return amp * np.cos(ph), amp * np.sin(ph)
+
+
+def basis_math(V, P, f, params: FitParams, L: int):
+    """fKK, fPEC and fSEC on the k basis vectors (Secs. 2.2-2.4).
+
+    V: (M, k) right singular vectors of A; P = A V = U S (N, k); f: (M,).
+    Returns the Basis pieces (without s / i_ref) and the row set q."""
+    V = np.asarray(V, F64)
+    P = np.asarray(P, F64)
+    f = np.asarray(f, F64)
+    M, k = V.shape
+    B = V.T / f  # V^T / f(w)
+    H_B = hilbert(B, L)  # fKK: H{V^T / f}, Eq. fKK (scaled form)
+    q = np.zeros(0, np.int64)
+    phi_pec_t = np.zeros((k, M))
+    if params.pec:
+        q = select_rows(P)
+        X = P[q]  # U_ss S
+        phi_ph = X @ H_B  # U_ss S H{V^T/f}
+        lam_als = params.als_lambda if params.als_lambda is not None else default_als_lambda(M)
+        phi_err = np.stack([als_baseline(r, lam_als, params.als_p, params.als_iters) for r in phi_ph])
+        lam_r = params.ridge_rel * float(np.sum(X * X)) / k
+        phi_pec_t = ridge(X, phi_err, lam_r)  # Eq. PEC_Ridge
+    H_phi = hilbert(phi_pec_t, L)
+    corrected = B + H_phi  # PEC-corrected log-amplitude basis, Eq. fPEC_K
+    if params.sec:
+        win = params.sg_window or default_sg_window(M)
+        v_sec_t = trend(corrected, params.sec_mode, win, params.sg_order)  # Eq. fSEC_VT
+    else:
+        v_sec_t = np.zeros((k, M))
+    c_amp = corrected - v_sec_t
+    c_ph = H_B - phi_pec_t
+    return B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph, q
+
+
+def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65536):
+    """Full fKK-EC (Fig. 1(b)): A, Gram, eigen, top-k, fKK, fPEC, fSEC, and the
+    reconstruction Eq. fKKEC.
+
+    The Gram matrix and P = A V are accumulated over row blocks of `chunk`
+    rows (the same sums in block order) so a large cube fits in memory.
+    Returns (Basis, P, result) where result holds Im/Re K for `out_rows`
+    (all rows if None), the eigenvalues and q."""
+    i_cars = np.asarray(i_cars)
+    N, M = i_cars.shape
+    k = params.k
+    L = params.pad_len or pad_len(M)
+    f = np.ones(M) if f is None else np.asarray(f, F64)
+    G = np.zeros((M, M))
+    for a in range(0, N, chunk):
+        A = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor)
+        G += A.T @ A
+    lam, Vall = eig_desc(G)
+    V = Vall[:, :k]
+    s = singular_from_eig(lam[:k])
+    P = np.empty((N, k))
+    for a in range(0, N, chunk):
+        P[a : a + chunk] = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor) @ V
+    B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph, q = basis_math(V, P, f, params, L)
+    basis = Basis(f, s, V, B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph,
+                  np.asarray(i_ref, F64), params, {"lam": lam, "q": q, "G": G})
+    rows = slice(None) if out_rows is None else out_rows
+    re, im = reconstruct(P[rows], c_amp, c_ph)
+    return basis, P, {"re": re, "im": im, "lam": lam, "q": q}
+
+
+def apply_projector(basis: Basis) -> np.ndarray:
+    """W with U_new S = A_new W: Eq. ML_Unew read as the ridge solution
+    U_new = A_new X^T (X X^T + lambda I)^-1, X = S V^T, which gives
+    U_new S = A_new V diag(s^2 / (s^2 + lambda))."""
+    s = basis.s
+    lam = basis.params.ml_lambda
+    return basis.V * (s**2 / (s**2 + lam))[None, :]
+
+
+def apply(basis: Basis, i_new, out_rows=None):
+    """ML:fKK-EC (Sec. 2.6): project new spectra on the trained basis and
+    reuse Eq. fKKEC.  Returns (Re K, Im K)."""
+    A = log_ratio(i_new if out_rows is None else np.asarray(i_new)[out_rows],
+                  basis.i_ref, basis.f, basis.params.ratio_floor)
+    P = A @ apply_projector(basis)
+    return reconstruct(P, basis.c_amp, basis.c_ph)
