@@ -1,0 +1,136 @@
+// Context, error and workspace management for the C ABI (include/fkk.h).
+#include <cstring>
+#include <new>
+
+#include "fkk_internal.h"
+
+namespace fkk {
+
+fkk_status fail(fkk_ctx* ctx, fkk_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+fkk_status cuda_check(fkk_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FKK_OK;
+  return fail(ctx, FKK_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+fkk_status bind(fkk_ctx* ctx) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  return cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+}
+
+void* workspace(fkk_ctx* ctx, const char* name, size_t bytes, fkk_status* st) {
+  *st = FKK_OK;
+  if (bytes == 0) bytes = 256;
+  auto& b = ctx->ws[name];
+  if (b.bytes >= bytes) return b.ptr;
+  size_t grow = bytes - b.bytes;
+  if (ctx->budget && ctx->used + grow > ctx->budget) {
+    *st = fail(ctx, FKK_ERR_BUDGET, "workspace '%s' needs %zu bytes; budget %zu, in use %zu", name,
+               bytes, ctx->budget, ctx->used);
+    return nullptr;
+  }
+  if (b.ptr) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      *st = cuda_check(ctx, e, "cudaDeviceSynchronize (workspace grow)");
+      return nullptr;
+    }
+    cudaFree(b.ptr);
+    ctx->used -= b.bytes;
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    *st = cuda_check(ctx, e, "cudaMalloc (workspace)");
+    return nullptr;
+  }
+  b.ptr = p;
+  b.bytes = bytes;
+  ctx->used += bytes;
+  return p;
+}
+
+}  // namespace fkk
+
+using namespace fkk;
+
+extern "C" {
+
+const char* fkk_strerror(fkk_status s) {
+  switch (s) {
+    case FKK_OK: return "FKK_OK";
+    case FKK_ERR_INVALID_ARG: return "FKK_ERR_INVALID_ARG";
+    case FKK_ERR_BUDGET: return "FKK_ERR_BUDGET";
+    case FKK_ERR_CUDA: return "FKK_ERR_CUDA";
+    case FKK_ERR_TIMEOUT: return "FKK_ERR_TIMEOUT";
+    case FKK_ERR_NOT_CONVERGED: return "FKK_ERR_NOT_CONVERGED";
+    case FKK_ERR_BAD_FILE: return "FKK_ERR_BAD_FILE";
+    case FKK_ERR_SHUTDOWN: return "FKK_ERR_SHUTDOWN";
+    default: return "FKK_ERR_UNKNOWN";
+  }
+}
+
+const char* fkk_version(void) { return "fkk 0.1 sm_103a"; }
+
+fkk_status fkk_create(fkk_ctx** out, int32_t device, size_t hbm_budget_bytes) {
+  if (!out) return FKK_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return FKK_ERR_INVALID_ARG;
+  fkk_ctx* c = new (std::nothrow) fkk_ctx();
+  if (!c) return FKK_ERR_INVALID_ARG;
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  fkk_status s = bind(c);
+  if (s == FKK_OK) s = cuda_check(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device), "sm count");
+  if (s == FKK_OK) s = cuda_check(c, cudaMalloc(&c->d_status, kStatusWords * sizeof(long long)), "cudaMalloc(status)");
+  if (s == FKK_OK) s = cuda_check(c, cudaMemset(c->d_status, 0, kStatusWords * sizeof(long long)), "cudaMemset(status)");
+  if (s != FKK_OK) {
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return FKK_OK;
+}
+
+fkk_status fkk_destroy(fkk_ctx* ctx) {
+  if (!ctx) return FKK_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->ws)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+  return FKK_OK;
+}
+
+const char* fkk_last_error(const fkk_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+size_t fkk_workspace_bytes(const fkk_ctx* ctx) { return ctx ? ctx->used : 0; }
+
+fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  long long h[kStatusWords];
+  FKK_CUDA(ctx, cudaStreamSynchronize(st));
+  FKK_CUDA(ctx, cudaMemcpy(h, ctx->d_status, sizeof h, cudaMemcpyDeviceToHost));
+  FKK_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof h));
+  if (clamped) *clamped = h[1];
+  return static_cast<fkk_status>(h[0]);
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/fkk.h"
+
+// Device status block, one per context (int64 words):
+//   [0] first device-side error code (0 = none)
+//   [1] number of ratios clamped to the floor
+//   [2] spare / diagnostic
+constexpr int kStatusWords = 4;
+
+struct fkk_ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t budget = 0;  // 0 = unlimited
+  size_t used = 0;
+  std::string last_error;
+  long long* d_status = nullptr;
+  struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+  };
+  std::map<std::string, Buf> ws;
+  std::recursive_mutex mu;
+};
+
+namespace fkk {
+
+// Record an error message on the context and return the status.
+fkk_status fail(fkk_ctx* ctx, fkk_status s, const char* fmt, ...);
+
+// Map a CUDA error to FKK_ERR_CUDA with a message (FKK_OK if no error).
+fkk_status cuda_check(fkk_ctx* ctx, cudaError_t e, const char* what);
+
+// Named grow-only workspace buffer.  Returns nullptr and records an error
+// (FKK_ERR_BUDGET or FKK_ERR_CUDA in *st) if it cannot be provided.  Growing
+// synchronises the device first, so buffers in use by queued work are safe.
+void* workspace(fkk_ctx* ctx, const char* name, size_t bytes, fkk_status* st);
+
+// Make the context's device current for this host thread.
+fkk_status bind(fkk_ctx* ctx);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int next_pow2(int64_t x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace fkk
+
+#define FKK_TRY(expr)                 \
+  do {                                \
+    fkk_status _s = (expr);           \
+    if (_s != FKK_OK) return _s;      \
+  } while (0)
+
+#define FKK_CUDA(ctx, expr) FKK_TRY(::fkk::cuda_check((ctx), (expr), #expr))
