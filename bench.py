@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the fKK-EC hot path on one GB300 (or N independent replicas).
+
+Workload: the paper-shaped image, 846 x 831 = 703,026 synthetic spectra x
+1,000 channels (30 Lorentzian species, Poisson + Gaussian noise at SNR 20,
+surrogate NRB with 5 % scale and 0.05 rad phase error), k = 40, fPEC and
+fSEC on, f(w) from the noise model.  One step = one fKK-EC fit of the cube
+plus its reconstruction (Im{K} for every spectrum), i.e. every stage of the
+factorised path: log ratio, Gram, eigensolve, projection, fKK / fPEC / fSEC
+on the basis, reconstruction.
+
+Printed (one JSON line, rank 0): value = fKK-EC spectra/s of the whole job,
+the per-stage breakdown, the roofline of the dominant stage, the same metric
+end to end through pinned host buffers (e2e), the FP64 CPU oracle on a
+bounded sample of the same cube (cpu_baseline), the per-spectrum KK and the
+ML apply throughput on the same cube, clocks sampled during the timed
+region, and the number of library kernels launched in it.
+
+--impl reference times the oracle itself (plain FP64 numpy) as the reference
+arm: each step is an oracle fit of a bounded sample of the same workload.
+Multi-GPU: one process per GPU, each fitting its own image (replicas only,
+weak scaling); the only cross-rank communication is the timing barrier and
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "img846x831_m1000"
+K_BASIS = 40
+METRIC = "fKK-EC spectra/s (fit + reconstruction)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / KK / apply / cpu baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fkk_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers --
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2005_07132_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+STAGE_KERNEL = {  # stage -> (kernel, sources, bound)
+    "transform": ("transform_kernel", ["fit_prep.cu", "common.cuh"], "hbm"),
+    "gram": ("gram_tc_kernel", ["gram.cu", "tc.cuh", "common.cuh"], "tensor"),
+    "eig": ("block_jacobi_kernel", ["eig.cu", "common.cuh"], "alu"),
+    "project": ("project_kernel", ["project.cu", "common.cuh"], "hbm"),
+    "basis": ("als_kernel", ["basis.cu", "fft.cuh", "common.cuh"], "alu"),
+    "recon": ("recon_kernel", ["recon.cu", "common.cuh"], "hbm"),
+}
+
+
+def algorithmic_work(stage, n, m, k, sweeps):
+    """Algorithmic bytes (hbm) or flops (tensor / alu) of one launch of the
+    stage's dominant kernel for n spectra, m channels, k basis vectors."""
+    mg = -(-m // 256) * 256
+    np_ = -(-n // 64) * 64
+    if stage == "transform":
+        return 4.0 * n * m + 2 * 2.0 * np_ * mg  # read I (fp32), write two bf16 terms
+    if stage == "gram":
+        return 3.0 * m * m * n  # symmetric Gram, three bf16 products per term
+    if stage == "eig":
+        mp = -(-m // 16) * 16
+        return 2.0 * 3 * mp * mp * 16 * (mp // 16) * (sweeps or 1) / 2  # block-Jacobi FMA per sweep x sweeps
+    if stage == "project":
+        return 2 * 2.0 * np_ * mg + 4.0 * n * k
+    if stage == "recon":
+        return 4.0 * n * m + 4.0 * n * k
+    return None
+
+
+def traffic_from_profiles(kernel, src_hash):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    taken on the current source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        e = t[kernel]
+        if e.get("source_hash") != src_hash:
+            return None
+        return e["dram_bytes_per_launch"] * e.get("scale", 1.0)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ arms --
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    from paper_2005_07132_gb300.synth import CONFIGS, make_cube
+
+    cube = make_cube(CONFIGS[WORKLOAD])
+    n_sample = 50_000
+    xi = cube.i_cars[:n_sample]
+    f = O.noise_scale(cube.i_cars.astype(np.float64).mean(0), cube.alpha, cube.sigma_g)
+    prm = O.FitParams(k=K_BASIS)
+    for _ in range(args.warmup):
+        O.fit(xi, cube.i_ref, prm, f=f)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.fit(xi, cube.i_ref, prm, f=f)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    cores = len(os.sched_getaffinity(0))
+    value = n_sample / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_spectra": n_sample, "n_channels": int(cube.i_cars.shape[1]),
+                   "k": K_BASIS, "sample": f"first {n_sample} spectra of the 703,026-spectrum cube"},
+        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores, "kind": "oracle",
+                         "sample": f"fit of the first {n_sample} spectra (fp64 numpy oracle)"},
+        "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(cube):
+    import numpy as np
+
+    import oracle as O
+
+    n_sample = 100_000
+    f = O.noise_scale(cube.i_cars.astype(np.float64).mean(0), cube.alpha, cube.sigma_g)
+    t0 = time.perf_counter()
+    O.fit(cube.i_cars[:n_sample], cube.i_ref, O.FitParams(k=K_BASIS), f=f)
+    t = time.perf_counter() - t0
+    return {"value": n_sample / t, "unit": "spectra/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"fp64 oracle fit + reconstruction of the first {n_sample} of 703,026 spectra "
+                      f"({t:.1f} s)"}
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2005_07132_gb300 as fk
+    from paper_2005_07132_gb300.synth import CONFIGS, make_cube
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = CONFIGS[WORKLOAD]
+    cube = make_cube(spec, image=rank)  # each rank fits its own image of the scene
+    n, m = cube.i_cars.shape
+    ctx = fk.Context(local)
+    st = torch.cuda.current_stream()
+    x = torch.from_numpy(cube.i_cars).cuda()
+    ref = torch.from_numpy(cube.i_ref).cuda()
+    out = torch.empty_like(x)
+    prm = fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g)
+
+    def step():
+        b, _, _ = fk.fkk_fit_basis(ctx, x, ref, prm, im_out=out, stream=st)
+        return b
+
+    bases = []
+    for _ in range(max(3, args.warmup)):
+        bases.append(step())
+    torch.cuda.synchronize()
+    for b in bases:
+        b.close()
+    bases.clear()
+    status, clamped = ctx.sync_status()
+
+    # ---- timed region (device-resident inputs) ----
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = fk.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stage_acc = {}
+    e0.record(st)
+    for _ in range(args.steps):
+        bases.append(step())
+        # stage events are recorded on the same stream; read after the loop
+    e1.record(st)
+    torch.cuda.synchronize()
+    launches = fk.launch_count() - l0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    stage_acc = ctx.stage_ms()  # last step's stages
+    sweeps = ctx.eig_sweeps()
+    status2, _ = ctx.sync_status()
+    ctx.set_timing(False)
+    for b in bases:
+        b.close()
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step / 1e3)
+
+    # ---- roofline of the dominant stage ----
+    pk = peaks()
+    stage = max(stage_acc, key=stage_acc.get)
+    kernel, srcs, bound = STAGE_KERNEL[stage]
+    work = algorithmic_work(stage, n, m, K_BASIS, sweeps[0])
+    t_s = stage_acc[stage] / 1e3
+    if bound == "hbm":
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        achieved = work / t_s / 1e9
+        unit = "GB/s"
+        peak_note = "measured hbm_gbs" if pk else "fallback"
+    elif bound == "tensor":
+        peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+        achieved = work * 2 / t_s / 1e12
+        unit = "TFLOP/s"
+        peak_note = "measured bf16_tflops_sustained" if pk else "fallback"
+    else:
+        peak = fp32_peak_tflops(clk.get("sm_max_mhz"))
+        achieved = work / t_s / 1e12
+        unit = "TFLOP/s"
+        peak_note = "fp32 ALU peak from 152 SMs x 128 lanes x 2 x max SM clock"
+    src_hash = source_hash(srcs)
+    roofline = {"stage": stage, "kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
+                "peak_source": peak_note, "unit": unit, "frac": achieved / peak,
+                "traffic": traffic_from_profiles(kernel, src_hash), "source_hash": src_hash}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_spectra": n, "n_channels": m, "k": K_BASIS, "pec": True, "sec": True,
+                   "noise": "poisson+gauss snr20", "l2": "inputs (2.81 GB) larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stage_ms": stage_acc, "eig_sweeps": {"fp32": sweeps[0], "fp64": sweeps[1]},
+        "device_status": int(status2), "clamped_ratios_per_fit": int(clamped) // max(1, max(3, args.warmup)),
+        "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+    }
+
+    if not args.no_extras:
+        # ---- e2e through pinned host buffers ----
+        xh = torch.from_numpy(cube.i_cars).pin_memory()
+        oh = torch.empty_like(xh).pin_memory()
+        xd = torch.empty_like(x)
+        refh = torch.from_numpy(cube.i_ref).pin_memory()
+        refd = torch.empty_like(ref)
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            refd.copy_(refh, non_blocking=True)
+            b, _, _ = fk.fkk_fit_basis(ctx, xd, refd, prm, im_out=out, stream=st)
+            oh.copy_(out, non_blocking=True)
+            return b
+
+        for _ in range(2):
+            bases.append(e2e_step())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(st)
+        for _ in range(args.steps):
+            bases.append(e2e_step())
+        e1.record(st)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        for b in bases:
+            b.close()
+        bases.clear()
+        line["e2e"] = {"value": world * n / (e2e_ms / 1e3), "unit": "spectra/s",
+                       "h2d_bytes_per_step": int(xh.numel() * 4 + refh.numel() * 4),
+                       "d2h_bytes_per_step": int(oh.numel() * 4), "ms_per_step": e2e_ms}
+
+        # ---- per-spectrum KK and ML apply on the same cube ----
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        kk_ms = timed(lambda: fk.kk_per_spectrum(ctx, x, ref, im_out=out, stream=st))
+        basis = step()
+        ap_ms = timed(lambda: fk.fkk_apply(ctx, basis, x, im_out=out, stream=st))
+        basis.close()
+        line["kk_per_spectrum"] = {"value": n / (kk_ms / 1e3), "unit": "spectra/s", "ms": kk_ms,
+                                   "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9}
+        line["apply"] = {"value": n / (ap_ms / 1e3), "unit": "spectra/s", "ms": ap_ms,
+                         "hbm_gbs": 8.0 * n * m / (ap_ms / 1e3) / 1e9}
+        if rank == 0 and world == 1:
+            line["cpu_baseline"] = cpu_baseline(cube)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

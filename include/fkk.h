@@ -54,6 +54,9 @@ const char* fkk_strerror(fkk_status s);
 /* Library version string, e.g. "fkk 0.1 sm_103a". */
 const char* fkk_version(void);
 
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t fkk_launch_count(void);
+
 /* ------------------------------------------------------------------ */
 /* Context                                                              */
 /* ------------------------------------------------------------------ */
@@ -84,6 +87,23 @@ size_t fkk_workspace_bytes(const fkk_ctx* ctx);
  * FKK_ERR_NOT_CONVERGED), else FKK_OK.  `clamped` may be NULL. */
 fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped);
 
+/* Synchronise `stream` and read (without clearing) the sweep counts of the
+ * last eigensolve: *sweeps32 of the fp32 block Jacobi over the Gram matrix,
+ * *sweeps64 of the fp64 Jacobi of its Rayleigh-Ritz refinement.  Either
+ * pointer may be NULL. */
+fkk_status fkk_eig_sweeps(fkk_ctx* ctx, void* stream, int32_t* sweeps32, int32_t* sweeps64);
+
+/* Turn per-stage timing of fkk_fit_basis on (1) or off (0).  When on, each
+ * fit records CUDA events on its stream at the boundaries of six stages:
+ * 0 transform (log ratio, split, channel sums), 1 Gram, 2 eigensolve,
+ * 3 projection and argmax/argmin, 4 basis math (fKK, fPEC, fSEC), 5
+ * reconstruction. */
+fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on);
+
+/* Milliseconds of the first n (<= 6) stages of the last timed fit;
+ * synchronises on its last event. */
+fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
+
 /* ------------------------------------------------------------------ */
 /* Conventional per-spectrum KK (Eq. KCARS with the surrogate, Eq. K)   */
 /* ------------------------------------------------------------------ */
@@ -107,6 +127,140 @@ fkk_status kk_per_spectrum(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra,
                            int32_t n_channels, int64_t ld, const float* i_ref,
                            int32_t pad_len, float ratio_floor, float* im_out,
                            float* re_out, int64_t ld_out, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* fKK-EC fit (Fig. 1(b); Secs. 2.2-2.5) and ML apply (Sec. 2.6)        */
+/* ------------------------------------------------------------------ */
+
+enum { FKK_SEC_SAVGOL = 0, FKK_SEC_MEAN = 1 };
+enum { FKK_PREC_BF16X3 = 0 /* fp32-accurate: 3 bf16 products per term */ };
+
+typedef struct {
+  int32_t k;            /* kept basis vectors, 1..80 */
+  int32_t pad_len;      /* Hilbert pad length: 0 = nextpow2(2M); power of two in [M, 4096] */
+  int32_t pec;          /* 1 = factorised phase-error correction (Sec. 2.3) */
+  int32_t sec;          /* 1 = factorised scale-error correction (Sec. 2.4) */
+  double als_lambda;    /* ALS smoothness of the detrend D{}; <= 0 selects 1e4 (M/1000)^4 */
+  double als_p;         /* ALS asymmetry (weight of points above the baseline), 0 < p < 1 */
+  int32_t als_iters;    /* ALS reweighting iterations (>= 1) */
+  double ridge_rel;     /* lambda of Eq. PEC_Ridge = ridge_rel * ||U_ss S||_F^2 / k (>= 0) */
+  int32_t sec_mode;     /* FKK_SEC_SAVGOL or FKK_SEC_MEAN (trendline M{} of Eq. fSEC_VT) */
+  int32_t sg_window;    /* odd Savitzky-Golay window <= M; 0 = largest odd <= M/2 */
+  int32_t sg_order;     /* Savitzky-Golay polynomial order, < window, <= 7 */
+  double ml_lambda;     /* ridge lambda of Eq. ML_Unew used by fkk_apply (>= 0) */
+  int32_t precision;    /* FKK_PREC_BF16X3 */
+  float ratio_floor;    /* I/I_ref is clamped to >= ratio_floor before the log (> 0) */
+  double noise_alpha;   /* Poisson multiplier alpha of f(w) (Sec. 2.2); used when f is NULL */
+  double noise_sigma_g; /* Gaussian sigma_g of f(w); alpha = sigma_g = 0 means f = 1 */
+  double eig_tol;       /* relative off-diagonal tolerance of the fp32 Jacobi sweeps; 0 = 1e-6 */
+  int32_t eig_max_sweeps; /* cap on the fp32 Jacobi sweeps; 0 = 40 */
+} fkk_fit_params;
+
+/* Defaults: k 20, pad_len 0, pec 1, sec 1, als_lambda 0 (auto), als_p 0.01,
+ * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
+ * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
+ * eig_tol 0 (1e-6), eig_max_sweeps 0 (40). */
+void fkk_fit_params_default(fkk_fit_params* p);
+
+/* Trained artefacts (Sec. 2.6: f, S, V, Phi_PEC, V_SEC) resident on the
+ * context's device.  Owned by the caller; release with fkk_basis_free. */
+typedef struct fkk_basis fkk_basis;
+
+/* Fit fKK-EC on a cube and optionally reconstruct it (Eq. fKKEC).
+ *   A   = f(w) * 1/2 ln(max(I_CARS/I_ref, floor))       (Sec. 2.2, scaled A)
+ *   A^T A = V diag(lambda) V^T (Jacobi eigensolve); s = sqrt(lambda_1..k);
+ *   P   = A V_k = U S;   q = argmax / argmin rows of each column of P
+ *   fKK: B = V^T/f, H{B};  fPEC: Eq. phi_err_USphi_b + Eq. PEC_Ridge;
+ *   fSEC: Eq. fSEC_VT;  Im{K} = exp(P C_amp) sin(P C_ph).
+ * i_cars: n_spectra x n_channels floats (stride ld); i_ref: n_channels floats;
+ * f_or_null: n_channels floats (f(w)), or NULL to use params->noise_* (both
+ * 0 means f = 1).  n_channels in [8, 2048]; 1 <= k <= min(80, n_channels);
+ * n_spectra >= k.  *out_basis receives the trained basis (required).
+ * im_out_or_null / re_out_or_null: n_spectra x n_channels outputs (stride
+ * ld_out) or NULL to skip the reconstruction.  Enqueued on `stream`;
+ * eigensolver non-convergence is reported by fkk_sync_status. */
+fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels, int64_t ld,
+                         const float* i_ref, const float* f_or_null, const fkk_fit_params* params,
+                         fkk_basis** out_basis, float* im_out_or_null, float* re_out_or_null, int64_t ld_out,
+                         void* stream);
+
+/* ML:fKK-EC (Sec. 2.6): U_new S = A_new V diag(s^2/(s^2+ml_lambda)) with the
+ * basis's f, I_ref and ratio floor (Eq. ML_Unew), then Eq. fKKEC with the
+ * trained C_amp, C_ph.  i_cars has basis n_channels columns.  re_out may be
+ * NULL.  Errors: FKK_ERR_INVALID_ARG, FKK_ERR_BUDGET, FKK_ERR_CUDA. */
+fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* basis, const float* i_cars, int64_t n_spectra, int64_t ld,
+                     float* im_out, float* re_out, int64_t ld_out, void* stream);
+
+/* Build a basis from HOST arrays (doubles): f (M), s (k), V (M x k), C_amp
+ * and C_ph (k x M), I_ref (M).  params supplies k, pad_len, ratio_floor and
+ * ml_lambda.  The arrays are copied; the call is synchronous. */
+fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t n_channels, const fkk_fit_params* params, const double* f,
+                                 const double* s, const double* v, const double* c_amp, const double* c_ph,
+                                 const double* i_ref, fkk_basis** out_basis);
+
+/* sizeof(fkk_fit_params) as compiled into the library (ABI check). */
+size_t fkk_fit_params_size(void);
+
+/* Release a basis (NULL is ok).  Synchronises the basis's device. */
+void fkk_basis_free(fkk_basis* basis);
+
+/* Shape of a basis.  Any output pointer may be NULL.  *nq (the number of
+ * sub-sampled rows of Eq. q_max/q_min) needs the fit to have completed and
+ * synchronises the device. */
+fkk_status fkk_basis_info(const fkk_basis* basis, int32_t* n_channels, int32_t* k, int32_t* pad_len, int32_t* nq);
+
+/* Copy one trained artefact to HOST memory as doubles (synchronous).
+ * which / element count:
+ *   FKK_ART_S        k        singular values s
+ *   FKK_ART_LAMBDA   k        eigenvalues of A^T A
+ *   FKK_ART_V        M*k      V_k, row-major M x k
+ *   FKK_ART_F        M        f(w)
+ *   FKK_ART_B, FKK_ART_H_B, FKK_ART_PHI_PEC, FKK_ART_H_PHI, FKK_ART_V_SEC,
+ *   FKK_ART_C_AMP, FKK_ART_C_PH      k*M each, row-major k x M
+ *   FKK_ART_Q        nq       sub-sampled row indices (sorted)
+ * `count` must equal the element count. */
+enum {
+  FKK_ART_S = 0, FKK_ART_LAMBDA, FKK_ART_V, FKK_ART_F, FKK_ART_B, FKK_ART_H_B, FKK_ART_PHI_PEC,
+  FKK_ART_H_PHI, FKK_ART_V_SEC, FKK_ART_C_AMP, FKK_ART_C_PH, FKK_ART_Q
+};
+fkk_status fkk_basis_get(const fkk_basis* basis, int32_t which, double* host_dst, size_t count);
+
+/* ------------------------------------------------------------------ */
+/* Pipeline steps, exposed for composition and step-by-step checking    */
+/* ------------------------------------------------------------------ */
+
+/* G = A^T A (fp64, n_channels x n_channels, row-major, device) with
+ * A = f * 1/2 ln(max(I/I_ref, floor)); f_or_null: device doubles or NULL. */
+fkk_status fkk_gram(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels, int64_t ld,
+                    const float* i_ref, float ratio_floor, const double* f_or_null, double* g_out, void* stream);
+
+/* Top-k eigenpairs of the symmetric fp64 G (device, m x m): lam_out (k,
+ * descending), v_out (m x k row-major), each column's largest-magnitude
+ * entry positive.  m in [2, 2048], 1 <= k <= min(80, m).  tol: relative
+ * tolerance of the fp32 Jacobi sweeps (0 = 1e-6); max_sweeps caps them
+ * (0 = 40); the fp64 refinement of the leading k + 32 vectors follows. */
+fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double tol, int32_t max_sweeps,
+                        double* lam_out, double* v_out, void* stream);
+
+/* P = A W (n x k fp32, row-major, device) for A as in fkk_gram and W
+ * (device, m x k doubles), through the same transformed-cube path as the
+ * fit; qmax/qmin (device int64, k each, or NULL) receive the argmax /
+ * argmin row of each column of P (ties to the lowest row). */
+fkk_status fkk_project(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels, int64_t ld,
+                       const float* i_ref, float ratio_floor, const double* f_or_null, const double* w, int32_t k,
+                       float* p_out, int64_t* qmax, int64_t* qmin, void* stream);
+
+/* fKK / fPEC / fSEC on the basis (device doubles): v (m x k), f_or_null (m),
+ * x_rows (nq x k, the rows P_q = U_ss S).  Outputs c_amp, c_ph (k x m). */
+fkk_status fkk_basis_math(fkk_ctx* ctx, int32_t m, int32_t k, const double* v, const double* f_or_null,
+                          const double* x_rows, int32_t nq, const fkk_fit_params* params, double* c_amp,
+                          double* c_ph, void* stream);
+
+/* Eq. fKKEC from P (n x k fp32) and C_amp, C_ph (k x m fp64): im_out (and
+ * re_out unless NULL) n x m with stride ld_out. */
+fkk_status fkk_reconstruct(fkk_ctx* ctx, const float* p, int64_t n_spectra, int32_t k, int32_t m,
+                           const double* c_amp, const double* c_ph, float* im_out, float* re_out, int64_t ld_out,
+                           void* stream);
 
 #ifdef __cplusplus
 }

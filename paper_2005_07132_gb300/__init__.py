@@ -7,6 +7,29 @@ sm_103a; this package is its thin Python binding (`_lib`), the in-tree build
 package does not load the library; the first binding call does, and raises
 if the library has not been built.
 """
-from ._lib import Context, FkkError, kk_per_spectrum, lib  # noqa: F401
+from ._lib import (  # noqa: F401
+    SEC_MEAN,
+    SEC_SAVGOL,
+    Basis,
+    Context,
+    FitParams,
+    FkkError,
+    fit_params,
+    fkk_apply,
+    fkk_basis_from_arrays,
+    fkk_basis_math,
+    fkk_eig_topk,
+    fkk_fit_basis,
+    fkk_gram,
+    fkk_project,
+    fkk_reconstruct,
+    kk_per_spectrum,
+    launch_count,
+    lib,
+)
 
-__all__ = ["Context", "FkkError", "kk_per_spectrum", "lib"]
+__all__ = [
+    "Basis", "Context", "FitParams", "FkkError", "SEC_MEAN", "SEC_SAVGOL", "fit_params", "fkk_apply",
+    "fkk_basis_from_arrays", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_gram", "fkk_project",
+    "fkk_reconstruct", "kk_per_spectrum", "launch_count", "lib",
+]

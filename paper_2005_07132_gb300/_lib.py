@@ -42,13 +42,64 @@ _SZ = C.c_size_t
 SIGNATURES = {
     "fkk_strerror": (C.c_char_p, [_I32]),
     "fkk_version": (C.c_char_p, []),
+    "fkk_launch_count": (C.c_uint64, []),
+    "fkk_set_timing": (_I32, [_P, _I32]),
+    "fkk_stage_ms": (_I32, [_P, C.POINTER(C.c_float), _I32]),
     "fkk_create": (_I32, [C.POINTER(_P), _I32, _SZ]),
     "fkk_destroy": (_I32, [_P]),
     "fkk_last_error": (C.c_char_p, [_P]),
     "fkk_workspace_bytes": (_SZ, [_P]),
     "fkk_sync_status": (_I32, [_P, _P, C.POINTER(_I64)]),
+    "fkk_eig_sweeps": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "kk_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _I32, _F32, _P, _P, _I64, _P]),
+    "fkk_fit_params_default": (None, [_P]),
+    "fkk_fit_params_size": (_SZ, []),
+    "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
+    "fkk_apply": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64, _P]),
+    "fkk_basis_free": (None, [_P]),
+    "fkk_basis_info": (_I32, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
+    "fkk_basis_get": (_I32, [_P, _I32, _P, _SZ]),
+    "fkk_basis_from_arrays": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, C.POINTER(_P)]),
+    "fkk_gram": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _P]),
+    "fkk_eig_topk": (_I32, [_P, _P, _I32, _I32, _F64, _I32, _P, _P, _P]),
+    "fkk_project": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _I32, _P, _P, _P, _P]),
+    "fkk_basis_math": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
+    "fkk_reconstruct": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
 }
+
+
+class FitParams(C.Structure):
+    """Mirror of fkk_fit_params (include/fkk.h)."""
+
+    _fields_ = [
+        ("k", C.c_int32), ("pad_len", C.c_int32), ("pec", C.c_int32), ("sec", C.c_int32),
+        ("als_lambda", C.c_double), ("als_p", C.c_double), ("als_iters", C.c_int32),
+        ("ridge_rel", C.c_double), ("sec_mode", C.c_int32), ("sg_window", C.c_int32),
+        ("sg_order", C.c_int32), ("ml_lambda", C.c_double), ("precision", C.c_int32),
+        ("ratio_floor", C.c_float), ("noise_alpha", C.c_double), ("noise_sigma_g", C.c_double),
+        ("eig_tol", C.c_double), ("eig_max_sweeps", C.c_int32),
+    ]
+
+
+SEC_SAVGOL, SEC_MEAN = 0, 1
+ART = {name: i for i, name in enumerate(
+    ["s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q"])}
+
+
+def launch_count() -> int:
+    """Kernels libfkk has launched in this process (fkk_launch_count)."""
+    return int(lib().fkk_launch_count())
+
+
+def fit_params(**kw) -> FitParams:
+    """fkk_fit_params_default(), then the given fields."""
+    p = FitParams()
+    lib().fkk_fit_params_default(C.byref(p))
+    for k_, v in kw.items():
+        if not hasattr(p, k_):
+            raise AttributeError(k_)
+        setattr(p, k_, v)
+    return p
 
 
 def lib():
@@ -68,9 +119,21 @@ def lib():
 
 
 def _ptr(t):
+    """Device pointer of a tensor; the C ABI takes dense row-major arrays, so
+    any tensor other than a 2-D row-strided view must be contiguous."""
     if t is None:
         return None
+    if t.dim() != 2 and not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if t.dim() == 2 and t.stride(1) != 1:
+        raise ValueError("2-D tensor must have unit column stride")
     return C.c_void_p(t.data_ptr())
+
+
+def _dense(t, name):
+    if t is not None and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
 
 
 def _stream(s):
@@ -111,6 +174,23 @@ class Context:
         st = lib().fkk_sync_status(self._h, _stream(stream), C.byref(n))
         return st, n.value
 
+    def set_timing(self, on: bool = True):
+        self.check(lib().fkk_set_timing(self._h, 1 if on else 0), "fkk_set_timing")
+
+    STAGES = ("transform", "gram", "eig", "project", "basis", "recon")
+
+    def stage_ms(self):
+        """{stage: ms} of the last timed fit (fkk_stage_ms)."""
+        arr = (C.c_float * 6)()
+        self.check(lib().fkk_stage_ms(self._h, arr, 6), "fkk_stage_ms")
+        return dict(zip(self.STAGES, [float(v) for v in arr]))
+
+    def eig_sweeps(self, stream=None):
+        """(fp32 Jacobi sweeps, fp64 refinement sweeps) of the last eigensolve."""
+        a, b = _I32(0), _I32(0)
+        self.check(lib().fkk_eig_sweeps(self._h, _stream(stream), C.byref(a), C.byref(b)), "fkk_eig_sweeps")
+        return a.value, b.value
+
     def close(self):
         if self._h:
             lib().fkk_destroy(self._h)
@@ -145,4 +225,163 @@ def kk_per_spectrum(ctx: Context, i_cars, i_ref, pad_len: int = 0, ratio_floor: 
     st = lib().kk_per_spectrum(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref), pad_len,
                                ratio_floor, _ptr(im_out), _ptr(re_out), im_out.stride(0), _stream(stream))
     ctx.check(st, "kk_per_spectrum")
+    return (im_out, re_out) if re_out is not None else im_out
+
+
+class Basis:
+    """Owns an fkk_basis (fkk_basis_free on close)."""
+
+    def __init__(self, handle, ctx: Context):
+        self._h = handle
+        self.ctx = ctx
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        m, k, L, nq = _I32(), _I32(), _I32(), _I32()
+        st = lib().fkk_basis_info(self._h, C.byref(m), C.byref(k), C.byref(L), C.byref(nq))
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_basis_info")
+        return {"n_channels": m.value, "k": k.value, "pad_len": L.value, "nq": nq.value}
+
+    def get(self, which: str):
+        """One artefact as a float64 numpy array (fkk_basis_get)."""
+        import numpy as np
+
+        inf = self.info()
+        m, k, nq = inf["n_channels"], inf["k"], inf["nq"]
+        shape = {"s": (k,), "lambda": (k,), "v": (m, k), "f": (m,), "q": (nq,)}.get(which, (k, m))
+        out = np.empty(shape, np.float64)
+        st = lib().fkk_basis_get(self._h, ART[which], out.ctypes.data_as(C.c_void_p), out.size)
+        if st != FKK_OK:
+            raise FkkError(st, f"fkk_basis_get({which})")
+        return out
+
+    def close(self):
+        if self._h:
+            lib().fkk_basis_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fkk_fit_basis(ctx: Context, i_cars, i_ref, params: FitParams, f=None, im_out=None, re_out=None,
+                  reconstruct: bool = True, stream=None):
+    """Fit fKK-EC (C: fkk_fit_basis).  Returns (Basis, im_out, re_out)."""
+    import torch
+
+    _check_2d(i_cars, "i_cars")
+    n, m = i_cars.shape
+    if reconstruct and im_out is None:
+        im_out = torch.empty((n, m), dtype=torch.float32, device=i_cars.device)
+    ld_out = im_out.stride(0) if im_out is not None else m
+    h = C.c_void_p()
+    st = lib().fkk_fit_basis(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref), _ptr(f),
+                             C.byref(params), C.byref(h), _ptr(im_out), _ptr(re_out), ld_out, _stream(stream))
+    ctx.check(st, "fkk_fit_basis")
+    return Basis(h, ctx), im_out, re_out
+
+
+def fkk_apply(ctx: Context, basis: Basis, i_cars, im_out=None, re_out=None, stream=None):
+    """ML:fKK-EC on new spectra (C: fkk_apply).  Returns im_out (re_out)."""
+    import torch
+
+    _check_2d(i_cars, "i_cars")
+    n, m = i_cars.shape
+    if im_out is None:
+        im_out = torch.empty((n, m), dtype=torch.float32, device=i_cars.device)
+    st = lib().fkk_apply(ctx.handle, basis.handle, _ptr(i_cars), n, i_cars.stride(0), _ptr(im_out), _ptr(re_out),
+                         im_out.stride(0), _stream(stream))
+    ctx.check(st, "fkk_apply")
+    return (im_out, re_out) if re_out is not None else im_out
+
+
+def fkk_basis_from_arrays(ctx: Context, params: FitParams, f, s, v, c_amp, c_ph, i_ref) -> Basis:
+    """Basis from host float64 arrays (C: fkk_basis_from_arrays)."""
+    import numpy as np
+
+    arrs = [np.ascontiguousarray(x, np.float64) for x in (f, s, v, c_amp, c_ph, i_ref)]
+    h = C.c_void_p()
+    st = lib().fkk_basis_from_arrays(ctx.handle, arrs[0].size, C.byref(params),
+                                     *[a.ctypes.data_as(C.c_void_p) for a in arrs], C.byref(h))
+    ctx.check(st, "fkk_basis_from_arrays")
+    return Basis(h, ctx)
+
+
+def fkk_gram(ctx: Context, i_cars, i_ref, ratio_floor: float = 1e-6, f=None, g_out=None, stream=None):
+    import torch
+
+    _check_2d(i_cars, "i_cars")
+    n, m = i_cars.shape
+    if g_out is None:
+        g_out = torch.empty((m, m), dtype=torch.float64, device=i_cars.device)
+    st = lib().fkk_gram(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref), ratio_floor, _ptr(f),
+                        _ptr(g_out), _stream(stream))
+    ctx.check(st, "fkk_gram")
+    return g_out
+
+
+def fkk_eig_topk(ctx: Context, g, k: int, tol: float = 0.0, max_sweeps: int = 0, stream=None):
+    import torch
+
+    _dense(g, "g")
+    m = g.shape[0]
+    lam = torch.empty(k, dtype=torch.float64, device=g.device)
+    v = torch.empty((m, k), dtype=torch.float64, device=g.device)
+    st = lib().fkk_eig_topk(ctx.handle, _ptr(g), m, k, tol, max_sweeps, _ptr(lam), _ptr(v), _stream(stream))
+    ctx.check(st, "fkk_eig_topk")
+    return lam, v
+
+
+def fkk_project(ctx: Context, i_cars, i_ref, w, ratio_floor: float = 1e-6, f=None, argext: bool = True,
+                stream=None):
+    import torch
+
+    _check_2d(i_cars, "i_cars")
+    _dense(w, "w")
+    _dense(f, "f")
+    n, m = i_cars.shape
+    k = w.shape[1]
+    p = torch.empty((n, k), dtype=torch.float32, device=i_cars.device)
+    qmax = torch.empty(k, dtype=torch.int64, device=i_cars.device) if argext else None
+    qmin = torch.empty(k, dtype=torch.int64, device=i_cars.device) if argext else None
+    st = lib().fkk_project(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref), ratio_floor, _ptr(f),
+                           _ptr(w), k, _ptr(p), _ptr(qmax), _ptr(qmin), _stream(stream))
+    ctx.check(st, "fkk_project")
+    return p, qmax, qmin
+
+
+def fkk_basis_math(ctx: Context, v, params: FitParams, x_rows=None, f=None, stream=None):
+    import torch
+
+    for t, nm in ((v, "v"), (x_rows, "x_rows"), (f, "f")):
+        _dense(t, nm)
+    m, k = v.shape
+    c_amp = torch.empty((k, m), dtype=torch.float64, device=v.device)
+    c_ph = torch.empty((k, m), dtype=torch.float64, device=v.device)
+    nq = 0 if x_rows is None else x_rows.shape[0]
+    st = lib().fkk_basis_math(ctx.handle, m, k, _ptr(v), _ptr(f), _ptr(x_rows), nq, C.byref(params), _ptr(c_amp),
+                              _ptr(c_ph), _stream(stream))
+    ctx.check(st, "fkk_basis_math")
+    return c_amp, c_ph
+
+
+def fkk_reconstruct(ctx: Context, p, c_amp, c_ph, im_out=None, re_out=None, stream=None):
+    import torch
+
+    for t, nm in ((p, "p"), (c_amp, "c_amp"), (c_ph, "c_ph")):
+        _dense(t, nm)
+    n, k = p.shape
+    m = c_amp.shape[1]
+    if im_out is None:
+        im_out = torch.empty((n, m), dtype=torch.float32, device=p.device)
+    st = lib().fkk_reconstruct(ctx.handle, _ptr(p), n, k, m, _ptr(c_amp), _ptr(c_ph), _ptr(im_out), _ptr(re_out),
+                               im_out.stride(0), _stream(stream))
+    ctx.check(st, "fkk_reconstruct")
     return (im_out, re_out) if re_out is not None else im_out

@@ -6,6 +6,8 @@
 
 namespace fkk {
 
+std::atomic<unsigned long long> g_launches{0};
+
 fkk_status fail(fkk_ctx* ctx, fkk_status s, const char* fmt, ...) {
   if (ctx) {
     char buf[512];
@@ -84,6 +86,8 @@ const char* fkk_strerror(fkk_status s) {
 
 const char* fkk_version(void) { return "fkk 0.1 sm_103a"; }
 
+uint64_t fkk_launch_count(void) { return g_launches.load(); }
+
 fkk_status fkk_create(fkk_ctx** out, int32_t device, size_t hbm_budget_bytes) {
   if (!out) return FKK_ERR_INVALID_ARG;
   int n = 0;
@@ -111,6 +115,8 @@ fkk_status fkk_destroy(fkk_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& kv : ctx->ws)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
   return FKK_OK;
@@ -131,6 +137,37 @@ fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped) {
   FKK_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof h));
   if (clamped) *clamped = h[1];
   return static_cast<fkk_status>(h[0]);
+}
+
+fkk_status fkk_eig_sweeps(fkk_ctx* ctx, void* stream, int32_t* s32, int32_t* s64) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  FKK_TRY(bind(ctx));
+  long long h[kStatusWords];
+  FKK_CUDA(ctx, cudaStreamSynchronize(as_stream(stream)));
+  FKK_CUDA(ctx, cudaMemcpy(h, ctx->d_status, sizeof h, cudaMemcpyDeviceToHost));
+  if (s32) *s32 = (int32_t)(h[2] & 0xffffffff);
+  if (s64) *s64 = (int32_t)(h[3] & 0xffffffff);
+  return FKK_OK;
+}
+
+fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->timing = on != 0;
+  ctx->ev_valid = false;
+  return FKK_OK;
+}
+
+fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n) {
+  if (!ctx || !ms || n < 1) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!ctx->ev_valid) return fail(ctx, FKK_ERR_INVALID_ARG, "no timed fit recorded");
+  FKK_TRY(bind(ctx));
+  FKK_CUDA(ctx, cudaEventSynchronize(ctx->ev[fkk_ctx::kStages]));
+  for (int i = 0; i < n && i < fkk_ctx::kStages; ++i)
+    FKK_CUDA(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+  return FKK_OK;
 }
 
 }  // extern "C"

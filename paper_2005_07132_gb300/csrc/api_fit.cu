@@ -1,0 +1,441 @@
+// C-ABI entry points of the fKK-EC fit, the ML apply, the basis object and
+// the individual pipeline steps (include/fkk.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fit.h"
+
+struct fkk_basis {
+  int device = 0;
+  int m = 0, k = 0, L = 0;
+  fkk_fit_params params{};
+  double* f = nullptr;      // m (always materialised, 1 when f = 1)
+  double* lam = nullptr;    // k
+  double* s = nullptr;      // k
+  double* v = nullptr;      // m x k
+  double* w = nullptr;      // m x k: V diag(s^2/(s^2+ml_lambda))
+  double* b = nullptr;      // k x m each below
+  double* h_b = nullptr;
+  double* phi_pec_t = nullptr;
+  double* h_phi = nullptr;
+  double* v_sec_t = nullptr;
+  double* c_amp = nullptr;
+  double* c_ph = nullptr;
+  int64_t* q = nullptr;     // up to 2k
+  int* nq = nullptr;        // device count
+  float* i_ref = nullptr;   // m
+  void* block = nullptr;    // single allocation backing all of the above
+};
+
+namespace fkk {
+namespace {
+
+__global__ void f_from_f32_kernel(const float* __restrict__ src, int m, double* __restrict__ f) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) f[j] = src ? (double)src[j] : 1.0;
+}
+
+__global__ void s_and_w_kernel(const double* __restrict__ lam, const double* __restrict__ v, int m, int k,
+                               double ml_lambda, double* __restrict__ s, double* __restrict__ w) {
+  const int i = blockIdx.x;
+  const double l = lam[i] > 0.0 ? lam[i] : 0.0;
+  const double shrink = (l + ml_lambda) > 0.0 ? l / (l + ml_lambda) : 0.0;
+  if (threadIdx.x == 0) s[i] = sqrt(l);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) w[(int64_t)j * k + i] = v[(int64_t)j * k + i] * shrink;
+}
+
+__global__ void copy_f32_kernel(const float* __restrict__ a, int m, float* __restrict__ b) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) b[j] = a[j];
+}
+
+fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n) {
+  if (p.k < 1 || p.k > 80 || p.k > m) return fail(ctx, FKK_ERR_INVALID_ARG, "k=%d must be in [1, min(80, M)]", p.k);
+  if (n < p.k) return fail(ctx, FKK_ERR_INVALID_ARG, "need at least k spectra");
+  if (p.pad_len && (p.pad_len < m || p.pad_len > 4096 || (p.pad_len & (p.pad_len - 1))))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "pad_len %d invalid", p.pad_len);
+  if (!p.pad_len && next_pow2(2 * (int64_t)m) > 4096)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "n_channels %d too large for the basis Hilbert transform", m);
+  if (!(p.als_p > 0.0 && p.als_p < 1.0) || p.als_iters < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "bad ALS parameters");
+  if (!(p.ridge_rel >= 0.0) || !(p.ml_lambda >= 0.0)) return fail(ctx, FKK_ERR_INVALID_ARG, "negative ridge");
+  if (p.sec_mode != FKK_SEC_SAVGOL && p.sec_mode != FKK_SEC_MEAN) return fail(ctx, FKK_ERR_INVALID_ARG, "bad sec_mode");
+  if (p.sec && p.sec_mode == FKK_SEC_SAVGOL) {
+    int w = p.sg_window;
+    if (w && (w % 2 == 0 || w > m || w <= p.sg_order)) return fail(ctx, FKK_ERR_INVALID_ARG, "bad sg_window");
+    if (p.sg_order < 0 || p.sg_order > 7) return fail(ctx, FKK_ERR_INVALID_ARG, "bad sg_order");
+  }
+  if (!(p.ratio_floor > 0.f)) return fail(ctx, FKK_ERR_INVALID_ARG, "ratio_floor must be > 0");
+  if (p.precision != FKK_PREC_BF16X3) return fail(ctx, FKK_ERR_INVALID_ARG, "unknown precision");
+  if (p.noise_alpha < 0.0 || p.noise_sigma_g < 0.0) return fail(ctx, FKK_ERR_INVALID_ARG, "negative noise parameter");
+  if (!(p.eig_tol >= 0.0 && p.eig_tol < 1.0)) return fail(ctx, FKK_ERR_INVALID_ARG, "eig_tol must be in [0, 1)");
+  if (p.eig_max_sweeps < 0 || p.eig_max_sweeps > 1000) return fail(ctx, FKK_ERR_INVALID_ARG, "bad eig_max_sweeps");
+  return FKK_OK;
+}
+
+BasisParams basis_params(const fkk_fit_params& p, int m, int L) {
+  BasisParams bp;
+  bp.m = m;
+  bp.k = p.k;
+  bp.L = L;
+  bp.pec = p.pec;
+  bp.sec = p.sec;
+  bp.als_lambda = p.als_lambda > 0.0 ? p.als_lambda : 1e4 * std::pow(m / 1000.0, 4);
+  bp.als_p = p.als_p;
+  bp.als_iters = p.als_iters;
+  bp.ridge_rel = p.ridge_rel;
+  bp.sec_mode = p.sec_mode;
+  int w = p.sg_window;
+  if (!w) {
+    w = m / 2;
+    if (w % 2 == 0) --w;
+    if (w < 3) w = 3;
+  }
+  bp.sg_window = w;
+  bp.sg_order = p.sg_order;
+  return bp;
+}
+
+fkk_basis* basis_alloc(fkk_ctx* ctx, int m, int k, fkk_status* st) {
+  fkk_basis* b = new (std::nothrow) fkk_basis();
+  if (!b) {
+    *st = FKK_ERR_INVALID_ARG;
+    return nullptr;
+  }
+  const size_t mk = (size_t)m * k;
+  size_t doubles = (size_t)m + 2 * k + 2 * mk + 7 * mk;
+  size_t bytes = doubles * 8 + (size_t)2 * k * 8 + 64 + (size_t)m * 4 + 256;
+  cudaError_t e = cudaMalloc(&b->block, bytes);
+  if (e != cudaSuccess) {
+    *st = cuda_check(ctx, e, "cudaMalloc(basis)");
+    delete b;
+    return nullptr;
+  }
+  double* d = (double*)b->block;
+  b->f = d; d += m;
+  b->lam = d; d += k;
+  b->s = d; d += k;
+  b->v = d; d += mk;
+  b->w = d; d += mk;
+  b->b = d; d += mk;
+  b->h_b = d; d += mk;
+  b->phi_pec_t = d; d += mk;
+  b->h_phi = d; d += mk;
+  b->v_sec_t = d; d += mk;
+  b->c_amp = d; d += mk;
+  b->c_ph = d; d += mk;
+  b->q = (int64_t*)d;
+  b->nq = (int*)(b->q + 2 * k);
+  b->i_ref = (float*)(reinterpret_cast<uint8_t*>(b->nq) + 64);
+  b->device = ctx->device;
+  b->m = m;
+  b->k = k;
+  *st = FKK_OK;
+  return b;
+}
+
+}  // namespace
+}  // namespace fkk
+
+using namespace fkk;
+
+extern "C" {
+
+void fkk_fit_params_default(fkk_fit_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->k = 20;
+  p->pad_len = 0;
+  p->pec = 1;
+  p->sec = 1;
+  p->als_lambda = 0.0;
+  p->als_p = 0.01;
+  p->als_iters = 20;
+  p->ridge_rel = 1e-3;
+  p->sec_mode = FKK_SEC_SAVGOL;
+  p->sg_window = 0;
+  p->sg_order = 2;
+  p->ml_lambda = 0.0;
+  p->precision = FKK_PREC_BF16X3;
+  p->ratio_floor = 1e-6f;
+  p->noise_alpha = 0.0;
+  p->noise_sigma_g = 0.0;
+  p->eig_tol = 0.0;
+  p->eig_max_sweeps = 0;
+}
+
+fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
+                         const float* f_or_null, const fkk_fit_params* params, fkk_basis** out_basis,
+                         float* im_out, float* re_out, int64_t ld_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!params || !out_basis || !i_cars || !i_ref) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_fit_basis: null argument");
+  if (m < 8 || m > 2048 || n < 1 || ld < m) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_fit_basis: bad sizes");
+  if ((im_out || re_out) && ld_out < m) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_fit_basis: bad ld_out");
+  FKK_TRY(check_params(ctx, *params, m, n));
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  const fkk_fit_params& p = *params;
+  const int k = p.k;
+  const int L = p.pad_len ? p.pad_len : next_pow2(2 * (int64_t)m);
+  fkk_status s;
+  fkk_basis* B = basis_alloc(ctx, m, k, &s);
+  if (!B) return s;
+  B->params = p;
+  B->L = L;
+  auto bail = [&](fkk_status e) {
+    cudaStreamSynchronize(st);
+    cudaFree(B->block);
+    delete B;
+    return e;
+  };
+  DtLayout D;
+  stage_mark(ctx, 0, st);
+  s = launch_transform(ctx, i_cars, n, m, ld, i_ref, p.ratio_floor, D, st);
+  if (s) return bail(s);
+  // f(w)
+  if (f_or_null) {
+    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(f_or_null, m, B->f);
+  } else if (p.noise_alpha > 0.0 || p.noise_sigma_g > 0.0) {
+    s = launch_noise_scale(ctx, D.sum_i, n, m, p.noise_alpha, p.noise_sigma_g, B->f, st);
+    if (s) return bail(s);
+  } else {
+    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(nullptr, m, B->f);
+  }
+  FKK_COUNT_LAUNCH(); copy_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_ref, m, B->i_ref);
+  double* G = (double*)workspace(ctx, "fit_gram", (size_t)m * m * 8, &s);
+  if (!G) return bail(s);
+  stage_mark(ctx, 1, st);
+  if ((s = launch_gram(ctx, D, B->f, G, st))) return bail(s);
+  stage_mark(ctx, 2, st);
+  if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st, nullptr, p.eig_tol, p.eig_max_sweeps))) return bail(s);
+  FKK_COUNT_LAUNCH(); s_and_w_kernel<<<k, 256, 0, st>>>(B->lam, B->v, m, k, p.ml_lambda, B->s, B->w);
+  float* P = (float*)workspace(ctx, "fit_p", (size_t)n * k * 4, &s);
+  if (!P) return bail(s);
+  int64_t* qm = (int64_t*)workspace(ctx, "fit_qext", (size_t)2 * k * 8, &s);
+  if (!qm) return bail(s);
+  stage_mark(ctx, 3, st);
+  if ((s = launch_project(ctx, D, B->v, B->f, k, P, qm, qm + k, st))) return bail(s);
+  stage_mark(ctx, 4, st);
+  int* nq_dev = (int*)workspace(ctx, "fit_nq", 64, &s);
+  if (!nq_dev) return bail(s);
+  double* xr = (double*)workspace(ctx, "fit_xrows", (size_t)2 * k * k * 8, &s);
+  if (!xr) return bail(s);
+  if ((s = launch_gather_q(ctx, qm, qm + k, k, P, B->q, nq_dev, xr, st))) return bail(s);
+  if ((s = cuda_check(ctx, cudaMemcpyAsync(B->nq, nq_dev, sizeof(int), cudaMemcpyDeviceToDevice, st), "nq"))) return bail(s);
+  BasisOut bo{B->c_amp, B->c_ph, B->b, B->h_b, B->phi_pec_t, B->h_phi, B->v_sec_t};
+  if ((s = launch_basis_math(ctx, basis_params(p, m, L), B->v, B->f, xr, 2 * k, bo, st))) return bail(s);
+  stage_mark(ctx, 5, st);
+  if (im_out) {
+    if ((s = launch_reconstruct(ctx, P, n, k, m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st))) return bail(s);
+  }
+  stage_mark(ctx, 6, st);
+  if ((s = cuda_check(ctx, cudaGetLastError(), "fkk_fit_basis"))) return bail(s);
+  *out_basis = B;
+  return FKK_OK;
+}
+
+fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int64_t n, int64_t ld, float* im_out,
+                     float* re_out, int64_t ld_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!B || !im_out) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null argument");
+  if (n < 0 || ld < B->m || ld_out < B->m) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: bad sizes");
+  if (n == 0) return FKK_OK;
+  if (!i_cars) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null input");
+  if (B->device != ctx->device) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: basis on another device");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  fkk_status s;
+  float* P = (float*)workspace(ctx, "apply_p", (size_t)n * B->k * 4, &s);
+  if (!P) return s;
+  FKK_TRY(launch_project_raw(ctx, i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, B->w, B->f, B->k, P, st));
+  return launch_reconstruct(ctx, P, n, B->k, B->m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st);
+}
+
+size_t fkk_fit_params_size(void) { return sizeof(fkk_fit_params); }
+
+fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* params, const double* f,
+                                 const double* sv, const double* v, const double* c_amp, const double* c_ph,
+                                 const double* i_ref, fkk_basis** out) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!params || !f || !sv || !v || !c_amp || !c_ph || !i_ref || !out || m < 8 || m > 2048)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_from_arrays: bad arguments");
+  FKK_TRY(check_params(ctx, *params, m, params->k));
+  FKK_TRY(bind(ctx));
+  const int k = params->k;
+  fkk_status s;
+  fkk_basis* B = basis_alloc(ctx, m, k, &s);
+  if (!B) return s;
+  B->params = *params;
+  B->L = params->pad_len ? params->pad_len : next_pow2(2 * (int64_t)m);
+  const size_t mk = (size_t)m * k;
+  std::vector<double> lam(k), w(mk);
+  for (int i = 0; i < k; ++i) lam[i] = sv[i] * sv[i];
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < k; ++i) {
+      const double l = lam[i];
+      const double shrink = (l + params->ml_lambda) > 0.0 ? l / (l + params->ml_lambda) : 0.0;
+      w[(size_t)j * k + i] = v[(size_t)j * k + i] * shrink;
+    }
+  std::vector<float> ir(m);
+  for (int j = 0; j < m; ++j) ir[j] = (float)i_ref[j];
+  int zero = 0;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cp(B->f, f, m * 8);
+  cp(B->s, sv, k * 8);
+  cp(B->lam, lam.data(), k * 8);
+  cp(B->v, v, mk * 8);
+  cp(B->w, w.data(), mk * 8);
+  cp(B->c_amp, c_amp, mk * 8);
+  cp(B->c_ph, c_ph, mk * 8);
+  cp(B->i_ref, ir.data(), m * 4);
+  cp(B->nq, &zero, sizeof zero);
+  if (e == cudaSuccess) e = cudaMemset(B->b, 0, 5 * mk * 8);  // b .. v_sec_t are not part of an imported basis
+  if (e != cudaSuccess) {
+    s = cuda_check(ctx, e, "fkk_basis_from_arrays");
+    cudaFree(B->block);
+    delete B;
+    return s;
+  }
+  B->params.pec = 0;  // no sub-sample to report
+  *out = B;
+  return FKK_OK;
+}
+
+void fkk_basis_free(fkk_basis* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  cudaFree(b->block);
+  delete b;
+}
+
+fkk_status fkk_basis_info(const fkk_basis* b, int32_t* m, int32_t* k, int32_t* L, int32_t* nq) {
+  if (!b) return FKK_ERR_INVALID_ARG;
+  if (m) *m = b->m;
+  if (k) *k = b->k;
+  if (L) *L = b->L;
+  if (nq) {
+    if (cudaSetDevice(b->device) != cudaSuccess) return FKK_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FKK_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, b->nq, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return FKK_ERR_CUDA;
+    *nq = b->params.pec ? v : 0;
+  }
+  return FKK_OK;
+}
+
+fkk_status fkk_basis_get(const fkk_basis* b, int32_t which, double* dst, size_t count) {
+  if (!b || !dst) return FKK_ERR_INVALID_ARG;
+  const size_t mk = (size_t)b->m * b->k;
+  const double* src = nullptr;
+  size_t want = 0;
+  switch (which) {
+    case FKK_ART_S: src = b->s; want = b->k; break;
+    case FKK_ART_LAMBDA: src = b->lam; want = b->k; break;
+    case FKK_ART_V: src = b->v; want = mk; break;
+    case FKK_ART_F: src = b->f; want = b->m; break;
+    case FKK_ART_B: src = b->b; want = mk; break;
+    case FKK_ART_H_B: src = b->h_b; want = mk; break;
+    case FKK_ART_PHI_PEC: src = b->phi_pec_t; want = mk; break;
+    case FKK_ART_H_PHI: src = b->h_phi; want = mk; break;
+    case FKK_ART_V_SEC: src = b->v_sec_t; want = mk; break;
+    case FKK_ART_C_AMP: src = b->c_amp; want = mk; break;
+    case FKK_ART_C_PH: src = b->c_ph; want = mk; break;
+    case FKK_ART_Q: break;
+    default: return FKK_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FKK_ERR_CUDA;
+  if (which == FKK_ART_Q) {
+    int nq = 0;
+    if (cudaMemcpy(&nq, b->nq, sizeof nq, cudaMemcpyDeviceToHost) != cudaSuccess) return FKK_ERR_CUDA;
+    if (!b->params.pec) nq = 0;
+    if (count != (size_t)nq) return FKK_ERR_INVALID_ARG;
+    std::vector<int64_t> tmp(nq > 0 ? nq : 1);
+    if (nq && cudaMemcpy(tmp.data(), b->q, nq * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return FKK_ERR_CUDA;
+    for (int i = 0; i < nq; ++i) dst[i] = (double)tmp[i];
+    return FKK_OK;
+  }
+  if (count != want) return FKK_ERR_INVALID_ARG;
+  return cudaMemcpy(dst, src, want * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess ? FKK_OK : FKK_ERR_CUDA;
+}
+
+fkk_status fkk_gram(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
+                    float floor_, const double* f, double* g_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!i_cars || !i_ref || !g_out || n < 1 || m < 1 || m > 2048 || ld < m || !(floor_ > 0.f))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_gram: bad arguments");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  DtLayout D;
+  FKK_TRY(launch_transform(ctx, i_cars, n, m, ld, i_ref, floor_, D, st));
+  return launch_gram(ctx, D, f, g_out, st);
+}
+
+fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double tol, int32_t max_sweeps,
+                        double* lam, double* v, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!g || !lam || !v || m < 2 || m > 2048 || k < 1 || k > 80 || k > m || !(tol >= 0.0 && tol < 1.0) || max_sweeps < 0 || max_sweeps > 1000)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_eig_topk: bad arguments");
+  FKK_TRY(bind(ctx));
+  return launch_eig_topk(ctx, g, m, k, lam, v, as_stream(stream), nullptr, tol, max_sweeps);
+}
+
+fkk_status fkk_project(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
+                       float floor_, const double* f, const double* w, int32_t k, float* p_out, int64_t* qmax,
+                       int64_t* qmin, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!i_cars || !i_ref || !w || !p_out || n < 1 || m < 1 || m > 2048 || ld < m || k < 1 || k > 80 ||
+      !(floor_ > 0.f) || ((qmax == nullptr) != (qmin == nullptr)))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_project: bad arguments");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  DtLayout D;
+  FKK_TRY(launch_transform(ctx, i_cars, n, m, ld, i_ref, floor_, D, st));
+  return launch_project(ctx, D, w, f, k, p_out, qmax, qmin, st);
+}
+
+fkk_status fkk_basis_math(fkk_ctx* ctx, int32_t m, int32_t k, const double* v, const double* f,
+                          const double* x_rows, int32_t nq, const fkk_fit_params* params, double* c_amp,
+                          double* c_ph, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!params || !v || !c_amp || !c_ph || m < 8 || m > 2048) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_math: bad arguments");
+  fkk_fit_params p = *params;
+  p.k = k;
+  FKK_TRY(check_params(ctx, p, m, k));
+  if (p.pec && (!x_rows || nq < 1 || nq > 2 * k)) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_math: bad x_rows / nq");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  fkk_status s;
+  int* nq_dev = (int*)workspace(ctx, "fit_nq", 64, &s);
+  if (!nq_dev) return s;
+  FKK_CUDA(ctx, cudaMemcpyAsync(nq_dev, &nq, sizeof(int), cudaMemcpyHostToDevice, st));
+  FKK_CUDA(ctx, cudaStreamSynchronize(st));
+  const int L = p.pad_len ? p.pad_len : next_pow2(2 * (int64_t)m);
+  BasisOut bo{c_amp, c_ph, nullptr, nullptr, nullptr, nullptr, nullptr};
+  return launch_basis_math(ctx, basis_params(p, m, L), v, f, x_rows, p.pec ? nq : 1, bo, st);
+}
+
+fkk_status fkk_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int32_t k, int32_t m, const double* c_amp,
+                           const double* c_ph, float* im, float* re, int64_t ld_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!p || !c_amp || !c_ph || !im || n < 0 || k < 1 || k > 80 || m < 1 || ld_out < m)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_reconstruct: bad arguments");
+  if (n == 0) return FKK_OK;
+  FKK_TRY(bind(ctx));
+  return launch_reconstruct(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,525 @@
+// fKK, fPEC and fSEC on the k basis vectors (Secs. 2.2-2.4), fp64, on the
+// device.  Sizes are small (k <= 80 rows, |q| <= 2k rows, M <= 2048
+// channels), so each step is a short kernel:
+//   B = V^T / f;  H_B = H{B}                                   (fKK, Eq. fKK)
+//   X = P_q;  Phi_ph = X H_B;  Phi_err = ALS baseline per row   (Eq. phi_err_USphi_b)
+//   Phi_PEC^T = (X^T X + lambda_r I)^-1 X^T Phi_err            (Eq. PEC_Ridge)
+//   H_Phi = H{Phi_PEC^T};  V_SEC^T = M{B + H_Phi}              (Eq. fSEC_VT)
+//   C_amp = B + H_Phi - V_SEC^T;  C_ph = H_B - Phi_PEC^T       (Eq. fKKEC)
+#include "common.cuh"
+#include "fft.cuh"
+#include "fit.h"
+
+namespace fkk {
+namespace {
+
+// ------------------------------------------------------------------ q ---
+__global__ void gather_q_kernel(const int64_t* __restrict__ qmax, const int64_t* __restrict__ qmin, int k,
+                                int64_t* __restrict__ q, int* __restrict__ nq) {
+  if (threadIdx.x != 0) return;
+  int64_t buf[160];
+  int n = 0;
+  for (int i = 0; i < k; ++i) { buf[n++] = qmax[i]; buf[n++] = qmin[i]; }
+  for (int a = 1; a < n; ++a) {  // insertion sort
+    int64_t v = buf[a];
+    int b = a - 1;
+    while (b >= 0 && buf[b] > v) { buf[b + 1] = buf[b]; --b; }
+    buf[b + 1] = v;
+  }
+  int u = 0;
+  for (int a = 0; a < n; ++a)
+    if (u == 0 || buf[a] != buf[u - 1]) buf[u++] = buf[a];
+  for (int a = 0; a < u; ++a) q[a] = buf[a];
+  *nq = u;
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ p, int k, const int64_t* __restrict__ q,
+                                   const int* __restrict__ nq, double* __restrict__ x) {
+  const int r = blockIdx.x;
+  if (r >= *nq) return;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) x[(int64_t)r * k + i] = (double)p[q[r] * k + i];
+}
+
+// ------------------------------------------------------------- Hilbert ---
+// One block per row: edge-replicated centred padding to L, FFT, -i sgn(m),
+// inverse FFT, crop.  rows_dev (optional) bounds the live rows.
+__global__ void hilbert_rows_f64_kernel(const double* __restrict__ x, int m, int L, double* __restrict__ h,
+                                        const int* __restrict__ rows_dev) {
+  extern __shared__ double2 zsm[];
+  const int row = blockIdx.x;
+  if (rows_dev && row >= *rows_dev) return;
+  double2* tw = zsm;
+  double2* b0 = zsm + L;
+  double2* b1 = b0 + L;
+  fill_twiddles_f64(tw, L);
+  const int left = (L - m) / 2;
+  const double* xr = x + (int64_t)row * m;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    int s = min(max(t - left, 0), m - 1);
+    b0[t] = make_double2(xr[s], 0.0);
+  }
+  __syncthreads();
+  int cur = fft_block_f64<-1>(b0, b1, L, tw, threadIdx.x, blockDim.x);
+  double2* X = cur ? b1 : b0;
+  double2* Y = cur ? b0 : b1;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) X[t] = hilbert_mult_f64(X[t], t, L);
+  __syncthreads();
+  int cur2 = fft_block_f64<+1>(X, Y, L, tw, threadIdx.x, blockDim.x);
+  double2* H = cur2 ? Y : X;
+  const double invL = 1.0 / (double)L;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) h[(int64_t)row * m + j] = H[left + j].x * invL;
+}
+
+// ---------------------------------------------------------- small ops ---
+__global__ void b_from_v_kernel(const double* __restrict__ v, const double* __restrict__ f, int m, int k,
+                                double* __restrict__ b) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) b[(int64_t)i * m + j] = v[(int64_t)j * k + i] / (f ? f[j] : 1.0);
+}
+
+// out[r, j] = sum_i X[r, i] Y[i, j]   (X rows x k, Y k x m)
+__global__ void small_gemm_kernel(const double* __restrict__ X, const double* __restrict__ Y, int k, int m,
+                                  double* __restrict__ out, const int* __restrict__ rows_dev) {
+  const int r = blockIdx.x;
+  if (rows_dev && r >= *rows_dev) return;
+  extern __shared__ double xs[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) xs[i] = X[(int64_t)r * k + i];
+  __syncthreads();
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < m; j += gridDim.y * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc = fma(xs[i], Y[(int64_t)i * m + j], acc);
+    out[(int64_t)r * m + j] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- ALS ---
+// Asymmetric least squares baseline of one row per block: repeat `iters`
+// times: solve (W + lam D2^T D2) z = W y, then w_i = p if y_i > z_i else
+// 1 - p (weights start at 1).  The pentadiagonal SPD system is solved in
+// fp64 as a block-tridiagonal system of 2 x 2 blocks (unknown pairs
+// (z_2i, z_2i+1)) by cyclic reduction: log2(P) levels of elimination and
+// back-substitution with the block rows of each level in parallel.  P is
+// the block count padded to a power of two with identity rows.
+
+// Band entries of D2^T D2 (D2 = (M-2) x M second differences): diagonal at j
+// and first off-diagonal (j, j+1); the second off-diagonal is 1 throughout.
+__device__ __forceinline__ double band0(int j, int m) {
+  double s = 0.0;
+  if (j <= m - 3) s += 1.0;
+  if (j >= 1 && j - 1 <= m - 3) s += 4.0;
+  if (j >= 2 && j - 2 <= m - 3) s += 1.0;
+  return s;
+}
+__device__ __forceinline__ double band1(int j, int m) {
+  double s = 0.0;
+  if (j >= 0 && j <= m - 3) s += -2.0;
+  if (j >= 1 && j - 1 <= m - 3) s += -2.0;
+  return s;
+}
+
+struct Blk {
+  double a, b, c, d;  // [[a, b], [c, d]]
+};
+__device__ __forceinline__ Blk bmul(const Blk& x, const Blk& y) {
+  return {fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c), fma(x.c, y.b, x.d * y.d)};
+}
+__device__ __forceinline__ Blk binv(const Blk& x) {
+  double det = fma(x.a, x.d, -x.b * x.c);
+  double r = 1.0 / det;
+  return {x.d * r, -x.b * r, -x.c * r, x.a * r};
+}
+__device__ __forceinline__ double2 bvec(const Blk& x, double2 v) {
+  return make_double2(fma(x.a, v.x, x.b * v.y), fma(x.c, v.x, x.d * v.y));
+}
+
+__global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_all, int m, int P, double lam, double p,
+                                                  int iters, double* __restrict__ z_all, const int* __restrict__ rows_dev) {
+  extern __shared__ double als_sm[];
+  const int row = blockIdx.x;
+  if (rows_dev && row >= *rows_dev) return;
+  Blk* A = reinterpret_cast<Blk*>(als_sm);
+  Blk* B = A + P;
+  Blk* C = B + P;
+  double2* D = reinterpret_cast<double2*>(C + P);
+  double* y = reinterpret_cast<double*>(D + P);
+  double* w = y + 2 * P;
+  double* z = w + 2 * P;
+  const double* yr = y_all + (int64_t)row * m;
+  for (int j = threadIdx.x; j < 2 * P; j += blockDim.x) {
+    y[j] = j < m ? yr[j] : 0.0;
+    w[j] = 1.0;
+  }
+  __syncthreads();
+  // matrix entry a(j, l) for |j - l| <= 2 (identity outside the signal)
+  auto ent = [&](int j, int l) -> double {
+    if (j < 0 || l < 0 || j >= 2 * P || l >= 2 * P) return 0.0;
+    if (j >= m || l >= m) return (j == l) ? 1.0 : 0.0;
+    int d = j - l;
+    if (d == 0) return w[j] + lam * band0(j, m);
+    if (d == 1 || d == -1) return lam * band1(min(j, l), m);
+    if (d == 2 || d == -2) return lam;
+    return 0.0;
+  };
+  for (int it = 0; it < iters; ++it) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      const int r0 = 2 * i, r1 = 2 * i + 1;
+      B[i] = {ent(r0, r0), ent(r0, r1), ent(r1, r0), ent(r1, r1)};
+      A[i] = {ent(r0, r0 - 2), ent(r0, r0 - 1), ent(r1, r0 - 2), ent(r1, r0 - 1)};
+      C[i] = {ent(r0, r1 + 1), ent(r0, r1 + 2), ent(r1, r1 + 1), ent(r1, r1 + 2)};
+      D[i] = make_double2(r0 < m ? w[r0] * y[r0] : 0.0, r1 < m ? w[r1] * y[r1] : 0.0);
+    }
+    __syncthreads();
+    // forward reduction
+    for (int s = 1; s < P; s *= 2) {
+      for (int t = threadIdx.x; t < P / (2 * s); t += blockDim.x) {
+        const int i = 2 * s * t + 2 * s - 1;
+        const int im = i - s, ip = i + s;
+        // alpha = -A_i B_im^-1, gamma = -C_i B_ip^-1
+        Blk ai = A[i], ci = C[i];
+        Blk bim_inv = binv(B[im]);
+        Blk alpha = bmul(ai, bim_inv);
+        alpha = {-alpha.a, -alpha.b, -alpha.c, -alpha.d};
+        Blk gamma = {0, 0, 0, 0};
+        if (ip < P) {
+          gamma = bmul(ci, binv(B[ip]));
+          gamma = {-gamma.a, -gamma.b, -gamma.c, -gamma.d};
+        }
+        Blk nb = B[i];
+        Blk t1 = bmul(alpha, C[im]);
+        nb = {nb.a + t1.a, nb.b + t1.b, nb.c + t1.c, nb.d + t1.d};
+        double2 nd = D[i];
+        double2 v1 = bvec(alpha, D[im]);
+        nd.x += v1.x;
+        nd.y += v1.y;
+        Blk na = bmul(alpha, A[im]);
+        Blk nc = {0, 0, 0, 0};
+        if (ip < P) {
+          Blk t2 = bmul(gamma, A[ip]);
+          nb = {nb.a + t2.a, nb.b + t2.b, nb.c + t2.c, nb.d + t2.d};
+          double2 v2 = bvec(gamma, D[ip]);
+          nd.x += v2.x;
+          nd.y += v2.y;
+          nc = bmul(gamma, C[ip]);
+        }
+        B[i] = nb;
+        D[i] = nd;
+        A[i] = na;
+        C[i] = nc;
+      }
+      __syncthreads();
+    }
+    // back-substitution (solutions overwrite D)
+    if (threadIdx.x == 0) D[P - 1] = bvec(binv(B[P - 1]), D[P - 1]);
+    __syncthreads();
+    for (int s = P / 2; s >= 1; s /= 2) {
+      for (int t = threadIdx.x; t < P / (2 * s); t += blockDim.x) {
+        const int i = 2 * s * t + s - 1;
+        double2 rhs = D[i];
+        if (i - s >= 0) {
+          double2 v = bvec(A[i], D[i - s]);
+          rhs.x -= v.x;
+          rhs.y -= v.y;
+        }
+        if (i + s < P) {
+          double2 v = bvec(C[i], D[i + s]);
+          rhs.x -= v.x;
+          rhs.y -= v.y;
+        }
+        D[i] = bvec(binv(B[i]), rhs);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      z[2 * i] = D[i].x;
+      z[2 * i + 1] = D[i].y;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] = (y[j] > z[j]) ? p : 1.0 - p;
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) z_all[(int64_t)row * m + j] = z[j];
+}
+
+// -------------------------------------------------------------- ridge ---
+// C = X^T X + lambda_r I with lambda_r = rel * ||X||_F^2 / k; Cholesky in
+// place (lower), one block.  X is nq x k.
+__global__ void ridge_chol_kernel(const double* __restrict__ X, const int* __restrict__ nq_dev, int k, double rel,
+                                  double* __restrict__ Lc) {
+  extern __shared__ double C[];
+  __shared__ double fro;
+  const int nq = *nq_dev;
+  if (threadIdx.x == 0) fro = 0.0;
+  __syncthreads();
+  double part = 0.0;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int a = t / k, b = t % k;
+    double s = 0.0;
+    for (int r = 0; r < nq; ++r) s = fma(X[(int64_t)r * k + a], X[(int64_t)r * k + b], s);
+    C[t] = s;
+    if (a == b) part += s;
+  }
+  atomicAdd(&fro, part);
+  __syncthreads();
+  const double lam = rel * fro / k;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) C[a * k + a] += lam;
+  __syncthreads();
+  // right-looking Cholesky
+  for (int c = 0; c < k; ++c) {
+    if (threadIdx.x == 0) C[c * k + c] = sqrt(C[c * k + c]);
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) C[r * k + c] /= C[c * k + c];
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+      int r = t / k, s = t % k;
+      if (r > c && s > c && s <= r) C[r * k + s] -= C[r * k + c] * C[s * k + c];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, s = t % k;
+    Lc[t] = (s <= r) ? C[t] : 0.0;
+  }
+}
+
+// R = X^T Phi_err (k x m), then solve (L L^T) out = R column by column.
+__global__ void ridge_solve_kernel(const double* __restrict__ X, const double* __restrict__ perr,
+                                   const int* __restrict__ nq_dev, int k, int m, const double* __restrict__ Lc,
+                                   double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int nq = *nq_dev;
+  double r[80];
+  for (int i = 0; i < k; ++i) r[i] = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    double e = perr[(int64_t)q * m + j];
+    for (int i = 0; i < k; ++i) r[i] = fma(X[(int64_t)q * k + i], e, r[i]);
+  }
+  for (int i = 0; i < k; ++i) {  // L y = r
+    double s = r[i];
+    for (int t = 0; t < i; ++t) s -= Lc[i * k + t] * r[t];
+    r[i] = s / Lc[i * k + i];
+  }
+  for (int i = k - 1; i >= 0; --i) {  // L^T x = y
+    double s = r[i];
+    for (int t = i + 1; t < k; ++t) s -= Lc[t * k + i] * r[t];
+    r[i] = s / Lc[i * k + i];
+  }
+  for (int i = 0; i < k; ++i) out[(int64_t)i * m + j] = r[i];
+}
+
+// ---------------------------------------------------------------- SEC ---
+// pinv of the window Vandermonde matrix V[t][p] = (t/h)^p, t = -h..h:
+// pinv = (V^T V)^-1 V^T, (order+1) x window.  One block.
+__global__ void sg_pinv_kernel(int window, int order, double* __restrict__ pinv) {
+  __shared__ double A[8][16];
+  __shared__ double part[8][8][32];
+  const int h = window / 2;
+  const int P = order + 1;
+  // moments sum_t x^q, x = t/h, q = 0..2 order: per-warp partial sums
+  double mom[15];
+  for (int q = 0; q < 2 * P - 1; ++q) mom[q] = 0.0;
+  for (int t = threadIdx.x; t < window; t += blockDim.x) {
+    double x = (double)(t - h) / h, pw = 1.0;
+    for (int q = 0; q < 2 * P - 1; ++q) {
+      mom[q] += pw;
+      pw *= x;
+    }
+  }
+  for (int q = 0; q < 2 * P - 1; ++q) {
+    double v = warp_sum(mom[q]);
+    if ((threadIdx.x & 31) == 0) part[q / 8][q % 8][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double M_[15];
+    for (int q = 0; q < 2 * P - 1; ++q) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += part[q / 8][q % 8][w];
+      M_[q] = sum;
+    }
+    for (int a = 0; a < P; ++a)
+      for (int b = 0; b < P; ++b) {
+        A[a][b] = M_[a + b];
+        A[a][P + b] = (a == b) ? 1.0 : 0.0;
+      }
+    for (int c = 0; c < P; ++c) {  // Gauss-Jordan (SPD, no pivoting needed)
+      double piv = A[c][c];
+      for (int b = 0; b < 2 * P; ++b) A[c][b] /= piv;
+      for (int a = 0; a < P; ++a)
+        if (a != c) {
+          double fct = A[a][c];
+          for (int b = 0; b < 2 * P; ++b) A[a][b] -= fct * A[c][b];
+        }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < window; t += blockDim.x) {
+    double tt = (double)(t - h) / h;
+    for (int a = 0; a < P; ++a) {
+      double s = 0.0, pw = 1.0;
+      for (int b = 0; b < P; ++b) {
+        s += A[a][P + b] * pw;
+        pw *= tt;
+      }
+      pinv[a * window + t] = s;
+    }
+  }
+}
+
+// Savitzky-Golay trendline of row r of x (k x m): interior points use the
+// centre coefficients (row 0 of pinv).  grid = (k, chunks).
+__global__ void sg_apply_kernel(const double* __restrict__ x, int m, int window, const double* __restrict__ pinv,
+                                double* __restrict__ out) {
+  const int r = blockIdx.x;
+  const int h = window / 2;
+  const double* xr = x + (int64_t)r * m;
+  for (int j = h + blockIdx.y * blockDim.x + threadIdx.x; j < m - h; j += gridDim.y * blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < window; ++t) s = fma(pinv[t], xr[j - h + t], s);
+    out[(int64_t)r * m + j] = s;
+  }
+}
+
+// The h points at each edge of row r: the polynomial fitted to the first /
+// last window (beta = pinv . window) evaluated there.  One block per row.
+__global__ void sg_edges_kernel(const double* __restrict__ x, int m, int window, int order,
+                                const double* __restrict__ pinv, double* __restrict__ out) {
+  __shared__ double beta[2][8];
+  __shared__ double red[8];
+  const int r = blockIdx.x;
+  const int h = window / 2;
+  const double* xr = x + (int64_t)r * m;
+  for (int side = 0; side < 2; ++side) {
+    const double* seg = side ? xr + (m - window) : xr;
+    for (int a = 0; a <= order; ++a) {
+      double s = 0.0;
+      for (int t = threadIdx.x; t < window; t += blockDim.x) s = fma(pinv[a * window + t], seg[t], s);
+      s = warp_sum(s);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tsum += red[q];
+        beta[side][a] = tsum;
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < 2 * h; t += blockDim.x) {
+    const int side = t >= h;
+    const int j = side ? m - h + (t - h) : t;
+    const double tt = side ? (double)(j - (m - 1 - h)) / h : (double)(j - h) / h;
+    double s = 0.0, pw = 1.0;
+    for (int a = 0; a <= order; ++a) {
+      s += beta[side][a] * pw;
+      pw *= tt;
+    }
+    out[(int64_t)r * m + j] = s;
+  }
+}
+
+__global__ void mean_rows_kernel(const double* __restrict__ x, int m, double* __restrict__ out) {
+  const int r = blockIdx.x;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) s += x[(int64_t)r * m + j];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    red[0] = t / m;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) out[(int64_t)r * m + j] = red[0];
+}
+
+__global__ void axpy3_kernel(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                             double sb, double sc, int64_t n, double* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  out[t] = a[t] + (b ? sb * b[t] : 0.0) + (c ? sc * c[t] : 0.0);
+}
+
+}  // namespace
+
+fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
+                           int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st) {
+  FKK_COUNT_LAUNCH(); gather_q_kernel<<<1, 32, 0, st>>>(qmax, qmin, k, q, nq_dev);
+  FKK_COUNT_LAUNCH(); gather_rows_kernel<<<2 * k, 32, 0, st>>>(p, k, q, nq_dev, x_rows);
+  return cuda_check(ctx, cudaGetLastError(), "gather_q launch");
+}
+
+static fkk_status hilbert_rows(fkk_ctx* ctx, const double* x, int rows, int m, int L, double* h, const int* rows_dev,
+                               cudaStream_t st) {
+  size_t smem = (size_t)3 * L * sizeof(double2);
+  FKK_CUDA(ctx, cudaFuncSetAttribute(hilbert_rows_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FKK_COUNT_LAUNCH(); hilbert_rows_f64_kernel<<<rows, 256, smem, st>>>(x, m, L, h, rows_dev);
+  return cuda_check(ctx, cudaGetLastError(), "hilbert_rows launch");
+}
+
+fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* v, const double* f,
+                             const double* x_rows, int nq_max, BasisOut out, cudaStream_t st) {
+  fkk_status s;
+  const int m = bp.m, k = bp.k, L = bp.L;
+  const size_t km = (size_t)k * m;
+  double* b = out.b ? out.b : (double*)workspace(ctx, "bm_b", km * 8, &s);
+  if (!b) return s;
+  double* hb = out.h_b ? out.h_b : (double*)workspace(ctx, "bm_hb", km * 8, &s);
+  if (!hb) return s;
+  double* phit = out.phi_pec_t ? out.phi_pec_t : (double*)workspace(ctx, "bm_phit", km * 8, &s);
+  if (!phit) return s;
+  double* hphi = out.h_phi ? out.h_phi : (double*)workspace(ctx, "bm_hphi", km * 8, &s);
+  if (!hphi) return s;
+  double* vsec = out.v_sec_t ? out.v_sec_t : (double*)workspace(ctx, "bm_vsec", km * 8, &s);
+  if (!vsec) return s;
+  double* corr = (double*)workspace(ctx, "bm_corr", km * 8, &s);
+  if (!corr) return s;
+
+  FKK_COUNT_LAUNCH(); b_from_v_kernel<<<k, 256, 0, st>>>(v, f, m, k, b);
+  FKK_TRY(hilbert_rows(ctx, b, k, m, L, hb, nullptr, st));
+  const unsigned ek = (unsigned)((km + 255) / 256);
+  if (bp.pec) {
+    const int* nq_dev = (const int*)workspace(ctx, "fit_nq", 64, &s);  // written by launch_gather_q
+    if (!nq_dev) return s;
+    double* phph = (double*)workspace(ctx, "bm_phph", (size_t)nq_max * m * 8, &s);
+    if (!phph) return s;
+    double* perr = (double*)workspace(ctx, "bm_perr", (size_t)nq_max * m * 8, &s);
+    if (!perr) return s;
+    double* lc = (double*)workspace(ctx, "bm_chol", (size_t)k * k * 8, &s);
+    if (!lc) return s;
+    FKK_COUNT_LAUNCH(); small_gemm_kernel<<<dim3(nq_max, 4), 256, k * sizeof(double), st>>>(x_rows, hb, k, m, phph, nq_dev);
+    int P = 1;
+    while (P < (m + 1) / 2) P *= 2;
+    size_t als_smem = (size_t)P * (3 * sizeof(Blk) + sizeof(double2)) + (size_t)6 * P * sizeof(double);
+    FKK_CUDA(ctx, cudaFuncSetAttribute(als_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)als_smem));
+    FKK_COUNT_LAUNCH(); als_kernel<<<nq_max, 256, als_smem, st>>>(phph, m, P, bp.als_lambda, bp.als_p, bp.als_iters, perr, nq_dev);
+    FKK_COUNT_LAUNCH(); ridge_chol_kernel<<<1, 256, (size_t)k * k * sizeof(double), st>>>(x_rows, nq_dev, k, bp.ridge_rel, lc);
+    FKK_COUNT_LAUNCH(); ridge_solve_kernel<<<(m + 63) / 64, 64, 0, st>>>(x_rows, perr, nq_dev, k, m, lc, phit);
+    FKK_CUDA(ctx, cudaGetLastError());
+    FKK_TRY(hilbert_rows(ctx, phit, k, m, L, hphi, nullptr, st));
+  } else {
+    FKK_CUDA(ctx, cudaMemsetAsync(phit, 0, km * 8, st));
+    FKK_CUDA(ctx, cudaMemsetAsync(hphi, 0, km * 8, st));
+  }
+  FKK_COUNT_LAUNCH(); axpy3_kernel<<<ek, 256, 0, st>>>(b, hphi, nullptr, 1.0, 0.0, (int64_t)km, corr);  // B + H_Phi
+  if (bp.sec) {
+    if (bp.sec_mode == 1) {
+      FKK_COUNT_LAUNCH(); mean_rows_kernel<<<k, 256, 0, st>>>(corr, m, vsec);
+    } else {
+      double* pinv = (double*)workspace(ctx, "bm_sgpinv", (size_t)(bp.sg_order + 1) * bp.sg_window * 8, &s);
+      if (!pinv) return s;
+      FKK_COUNT_LAUNCH(); sg_pinv_kernel<<<1, 256, 0, st>>>(bp.sg_window, bp.sg_order, pinv);
+      FKK_COUNT_LAUNCH(); sg_apply_kernel<<<dim3(k, (m + 255) / 256), 256, 0, st>>>(corr, m, bp.sg_window, pinv, vsec);
+      FKK_COUNT_LAUNCH(); sg_edges_kernel<<<k, 256, 0, st>>>(corr, m, bp.sg_window, bp.sg_order, pinv, vsec);
+    }
+  } else {
+    FKK_CUDA(ctx, cudaMemsetAsync(vsec, 0, km * 8, st));
+  }
+  FKK_COUNT_LAUNCH(); axpy3_kernel<<<ek, 256, 0, st>>>(corr, vsec, nullptr, -1.0, 0.0, (int64_t)km, out.c_amp);
+  FKK_COUNT_LAUNCH(); axpy3_kernel<<<ek, 256, 0, st>>>(hb, phit, nullptr, -1.0, 0.0, (int64_t)km, out.c_ph);
+  return cuda_check(ctx, cudaGetLastError(), "basis math launch");
+}
+
+}  // namespace fkk

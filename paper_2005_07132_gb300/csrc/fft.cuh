@@ -143,4 +143,58 @@ __device__ __forceinline__ float2 hilbert_mult(float2 z, int m, int L) {
   return (2 * m < L) ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
 }
 
+// ---------------------------------------------------------------- fp64 ---
+// Double-precision variants for the k basis vectors (a few rows of length L).
+__device__ __forceinline__ double2 z_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 z_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// One radix-2 Stockham pass in double precision (same indexing as above).
+template <int SIGN>
+__device__ __forceinline__ void stockham_pass2_f64(const double2* __restrict__ x, double2* __restrict__ y, int L,
+                                                   int Ns, const double2* __restrict__ tw, int t0, int nt) {
+  const int LR = L / 2;
+  const int tws = L / (Ns * 2);
+  for (int j = t0; j < LR; j += nt) {
+    const int k = j & (Ns - 1);
+    double2 a = x[j], b = x[j + LR];
+    if (Ns > 1) {
+      double2 w = tw[k * tws];
+      if (SIGN > 0) w.y = -w.y;
+      b = z_mul(b, w);
+    }
+    const int base = (j - k) * 2 + k;
+    y[base] = z_add(a, b);
+    y[base + Ns] = z_sub(a, b);
+  }
+}
+
+template <int SIGN>
+__device__ __forceinline__ int fft_block_f64(double2* buf0, double2* buf1, int L, const double2* tw, int t0,
+                                             int nt) {
+  double2* bufs[2] = {buf0, buf1};
+  int cur = 0;
+  for (int Ns = 1; Ns < L; Ns *= 2) {
+    stockham_pass2_f64<SIGN>(bufs[cur], bufs[cur ^ 1], L, Ns, tw, t0, nt);
+    cur ^= 1;
+    __syncthreads();
+  }
+  return cur;
+}
+
+__device__ __forceinline__ void fill_twiddles_f64(double2* tw, int L) {
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)L, &s, &c);
+    tw[t] = make_double2(c, s);
+  }
+}
+
+__device__ __forceinline__ double2 hilbert_mult_f64(double2 z, int m, int L) {
+  if (m == 0 || 2 * m == L) return make_double2(0.0, 0.0);
+  return (2 * m < L) ? make_double2(z.y, -z.x) : make_double2(-z.y, z.x);
+}
+
 }  // namespace fkk

@@ -1,0 +1,108 @@
+// Internal launchers of the fKK-EC fit pipeline (host side).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "fkk_internal.h"
+
+namespace fkk {
+
+// Channel-major transformed cube: D^T_hi / D^T_lo are mg x np bf16 arrays
+// (row = channel, contiguous along spectra), rows >= m and columns >= n are 0.
+struct DtLayout {
+  int64_t n = 0, np = 0;  // spectra, padded to a multiple of 64
+  int m = 0, mg = 0;      // channels, padded to a multiple of 256
+  __nv_bfloat16* dt_hi = nullptr;
+  __nv_bfloat16* dt_lo = nullptr;
+  float* c = nullptr;        // per-channel shift (m)
+  double* sum_d = nullptr;   // sum_n d[n, j] (m)
+  double* sum_i = nullptr;   // sum_n I[n, j] (m)
+};
+
+struct TransformArgs {
+  const float* i_cars;
+  int64_t n;
+  int m;
+  int64_t ld;
+  const float* i_ref;
+  float floor_;
+  const float* c;
+  int64_t np;
+  __nv_bfloat16* dt_hi;
+  __nv_bfloat16* dt_lo;
+  double* part_d;
+  double* part_i;
+  long long* status;
+};
+
+fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                            const float* i_ref, float floor_, DtLayout& L, cudaStream_t st);
+
+// G = diag(f) (D^T D + s c^T + c s^T + N c c^T) diag(f), fp64, m x m (ld m).
+// f == nullptr means f = 1.
+fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double* g, cudaStream_t st);
+
+// f(w) = 2 <I> / sqrt(alpha <I> + sigma_g^2) from the channel sums of I.
+fkk_status launch_noise_scale(fkk_ctx* ctx, const double* sum_i, int64_t n, int m, double alpha,
+                              double sigma_g, double* f, cudaStream_t st);
+
+// Top-k eigenpairs of the symmetric m x m fp64 G: lam (k, descending) and
+// V (m x k, row-major), each column's largest-magnitude entry positive.
+// *sweeps_out (host pointer, optional) receives the Jacobi sweep count once
+// the stream reaches it.
+fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* lam, double* v,
+                           cudaStream_t st, int* sweeps_out, double tol32 = 0.0, int max_sweeps32 = 0);
+
+// P = A W (n x k fp32, ld k) from the transformed cube, with A = (d + c) f
+// folded into W: P[n,i] = sum_j d[n,j] Wf[j,i] + o_i, Wf = f W, o = c^T Wf.
+// Per column of P the argmax / argmin row (ties to the lowest row) goes to
+// qmax / qmin (device, k each).  Optional outputs may be null.
+fkk_status launch_project(fkk_ctx* ctx, const DtLayout& L, const double* w, const double* f, int k, float* p,
+                          int64_t* qmax, int64_t* qmin, cudaStream_t st);
+
+// P = A W from the raw cube (for new data): A = f * 1/2 ln(max(I/I_ref, floor)).
+fkk_status launch_project_raw(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                              const float* i_ref, float floor_, const double* w, const double* f, int k,
+                              float* p, cudaStream_t st);
+
+// Basis math (fKK / fPEC / fSEC on the k vectors), all fp64, on the device.
+struct BasisParams {
+  int m, k, L;
+  int pec, sec;
+  double als_lambda, als_p;
+  int als_iters;
+  double ridge_rel;
+  int sec_mode;  // 0 Savitzky-Golay, 1 mean
+  int sg_window, sg_order;
+};
+// v: m x k (row-major); f: m; x_rows: nq x k (P_q, fp64, row-major, device).
+// Outputs (device, k x m row-major): c_amp, c_ph, and the pieces b, h_b,
+// phi_pec_t, h_phi, v_sec_t when the pointers are non-null.
+struct BasisOut {
+  double* c_amp;
+  double* c_ph;
+  double* b;
+  double* h_b;
+  double* phi_pec_t;
+  double* h_phi;
+  double* v_sec_t;
+};
+fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* v, const double* f,
+                             const double* x_rows, int nq, BasisOut out, cudaStream_t st);
+
+// q = sorted unique(qmax U qmin) (device int64, up to 2k), count to *nq_dev;
+// x_rows[r, :] = (double) P[q[r], :].
+fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
+                           int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st);
+
+// Out = exp(P C_amp) sin(P C_ph) (and cos for re_out), P n x k fp32.
+fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                              const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
+
+// Tensor map helper (driver entry point fetched once).
+fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,
+                        uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                        CUtensorMapSwizzle swz);
+
+}  // namespace fkk

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -31,9 +33,18 @@ struct fkk_ctx {
   };
   std::map<std::string, Buf> ws;
   std::recursive_mutex mu;
+  // optional per-stage timing of the fit (CUDA events on the fit's stream)
+  bool timing = false;
+  static constexpr int kStages = 6;  // transform, gram, eig, project, basis, recon
+  cudaEvent_t ev[kStages + 1] = {};
+  bool ev_valid = false;
 };
 
 namespace fkk {
+
+// Number of kernels this library has launched (process-wide).
+extern std::atomic<unsigned long long> g_launches;
+#define FKK_COUNT_LAUNCH() (::fkk::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // Record an error message on the context and return the status.
 fkk_status fail(fkk_ctx* ctx, fkk_status s, const char* fmt, ...);
@@ -50,6 +61,14 @@ void* workspace(fkk_ctx* ctx, const char* name, size_t bytes, fkk_status* st);
 fkk_status bind(fkk_ctx* ctx);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Record the boundary event `i` of the fit's stages when timing is on.
+inline void stage_mark(fkk_ctx* ctx, int i, cudaStream_t st) {
+  if (!ctx->timing) return;
+  if (!ctx->ev[i]) cudaEventCreate(&ctx->ev[i]);
+  cudaEventRecord(ctx->ev[i], st);
+  if (i == fkk_ctx::kStages) ctx->ev_valid = true;
+}
 
 inline int next_pow2(int64_t x) {
   int p = 1;

@@ -1,0 +1,264 @@
+// Gram matrix of the transformed cube on the 5th-generation tensor cores.
+//
+// G_d = D^T D over all spectra, D = hi + lo (two bf16 terms), computed as
+// hi.hi + hi.lo + lo.hi with fp32 accumulation in TMEM (relative error of a
+// product about 2^-17; the lo.lo term is below that).  Output tiles are
+// 128 (rows i) x 256 (columns j) covering the upper triangle (i-block 128*ib
+// < 256*(jb+1)); the contraction over spectra is split into `splits`
+// contiguous ranges, one CTA per (tile, split), and the fp32 partial tiles
+// are summed in fp64 in a fixed order by the assemble kernel, which also
+// adds the shift terms and the f(w) scaling.
+//
+// CTA = 4 warps.  Warp 0 lane 0 issues TMA loads of 64-spectrum K-blocks
+// (A: 128 channels, B: 256 channels, hi and lo) into a 2-stage ring; warp 1
+// lane 0 issues tcgen05.mma (M=128, N=256, K=16) from shared memory into a
+// 256-column TMEM accumulator; after the last K-block all 4 warps read the
+// accumulator (one TMEM lane per row) and store the partial tile.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "fit.h"
+#include "tc.cuh"
+
+namespace fkk {
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,
+                        uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                        CUtensorMapSwizzle swz) {
+  std::call_once(g_encode_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return fail(ctx, FKK_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, FKK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return FKK_OK;
+}
+
+namespace {
+
+constexpr int kBK = 64;                       // spectra per K-block (128 bytes of bf16)
+constexpr int kTileM = 128, kTileN = 256;
+constexpr int kStages = 2;
+constexpr uint32_t kABytes = kTileM * kBK * 2;  // 16 KB per term
+constexpr uint32_t kBBytes = kTileN * kBK * 2;  // 32 KB per term
+constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr size_t kGramSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+struct GramArgs {
+  int mb;        // row blocks of 128
+  int ntiles;
+  int64_t nkb;   // K-blocks of 64 spectra
+  int splits;
+  float* partial;  // [splits][ntiles][128][256]
+  long long* status;
+};
+
+// tile t -> (ib, jb) enumerating jb = 0, 1, ... and ib < min(2 (jb + 1), mb)
+__host__ __device__ inline void gram_tile(int t, int mb, int& ib, int& jb) {
+  jb = 0;
+  for (;;) {
+    int cnt = 2 * (jb + 1) < mb ? 2 * (jb + 1) : mb;
+    if (t < cnt) { ib = t; return; }
+    t -= cnt;
+    ++jb;
+  }
+}
+
+__global__ void __launch_bounds__(128, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tm_a_hi, const __grid_constant__ CUtensorMap tm_a_lo,
+                   const __grid_constant__ CUtensorMap tm_b_hi, const __grid_constant__ CUtensorMap tm_b_lo,
+                   GramArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int fail_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ib, jb;
+  gram_tile(blockIdx.x, p.mb, ib, jb);
+  const int split = blockIdx.y;
+  const int64_t kb0 = p.nkb * split / p.splits;
+  const int64_t kb1 = p.nkb * (split + 1) / p.splits;
+  const int nk = (int)(kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    fail_s = 0;
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tm_a_hi);
+    tc::prefetch_tmap(&tm_a_lo);
+    tc::prefetch_tmap(&tm_b_hi);
+    tc::prefetch_tmap(&tm_b_lo);
+  }
+  if (warp == 2) tc::tmem_alloc(tmem_slot, 256);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t taddr = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (i / kStages) & 1;
+      if (!tc::mbar_wait(&empty[s], ph ^ 1)) { fail_s = 1; break; }
+      uint8_t* st = smem + s * kStageBytes;
+      tc::mbar_arrive_expect_tx(&full[s], kStageBytes);
+      const int x = (int)((kb0 + i) * kBK);
+      tc::tma_load_2d(st, &tm_a_hi, &full[s], x, ib * kTileM);
+      tc::tma_load_2d(st + kABytes, &tm_a_lo, &full[s], x, ib * kTileM);
+      tc::tma_load_2d(st + 2 * kABytes, &tm_b_hi, &full[s], x, jb * kTileN);
+      tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tm_b_lo, &full[s], x, jb * kTileN);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
+    bool ok = true;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = (i / kStages) & 1;
+      if (!tc::mbar_wait(&full[s], ph)) { ok = false; fail_s = 1; break; }
+      tc::tc_fence_after();
+      const uint32_t a_hi = tc::smem_u32(smem + s * kStageBytes);
+      const uint32_t a_lo = a_hi + kABytes;
+      const uint32_t b_hi = a_hi + 2 * kABytes;
+      const uint32_t b_lo = b_hi + kBBytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint32_t off = kk * 32;  // 16 bf16 along K
+        tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_hi + off), tc::sdesc_kmajor_sw128(b_hi + off), idesc,
+                     (i > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_hi + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
+        tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_hi + off), idesc, 1u);
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    if (ok) tc::mma_commit(done);
+  }
+  __syncthreads();  // fail_s written by the producer / MMA lanes is visible below
+
+  // epilogue: every warp reads its 32 TMEM lanes (rows) x 256 columns
+  bool have = (nk > 0);
+  if (have) {
+    if (!tc::mbar_wait(done, 0)) {
+      have = false;
+      fail_s = 1;
+    }
+  }
+  tc::tc_fence_after();
+  const int row = warp * 32 + lane;
+  float* out = p.partial + (((int64_t)split * p.ntiles + blockIdx.x) * kTileM + row) * kTileN;
+  const bool failed = fail_s != 0;
+  for (int c = 0; c < kTileN / 32; ++c) {
+    float v[32];
+    if (have && !failed) {
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + c * 32, v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = 0.f;
+    }
+    float4* o4 = reinterpret_cast<float4*>(out + c * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  if (failed && threadIdx.x == 0) record_error(p.status, kErrTimeout);
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(taddr, 256);
+}
+
+// Sum partial tiles (fixed split order, fp64), add the shift terms, scale by
+// f, write both triangles of the m x m matrix.
+__global__ void gram_assemble_kernel(const float* __restrict__ partial, int splits, int ntiles, int mb, int m,
+                                     int64_t n, const float* __restrict__ c, const double* __restrict__ sd,
+                                     const double* __restrict__ f, double* __restrict__ g) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j >= m || j < i) return;
+  const int ib = i / kTileM, jb = j / kTileN;
+  int base = 0;
+  for (int q = 0; q < jb; ++q) base += (2 * (q + 1) < mb ? 2 * (q + 1) : mb);
+  const int tile = base + ib;
+  const int64_t off = ((int64_t)tile * kTileM + (i - ib * kTileM)) * kTileN + (j - jb * kTileN);
+  const int64_t tstride = (int64_t)ntiles * kTileM * kTileN;
+  double acc = 0.0;
+  for (int s = 0; s < splits; ++s) acc += (double)partial[s * tstride + off];
+  const double ci = c[i], cj = c[j];
+  acc += sd[i] * cj + ci * sd[j] + (double)n * ci * cj;
+  if (f) acc *= f[i] * f[j];
+  g[(int64_t)i * m + j] = acc;
+  g[(int64_t)j * m + i] = acc;
+}
+
+__global__ void noise_scale_kernel(const double* __restrict__ sum_i, int64_t n, int m, double alpha,
+                                   double sigma_g, double* __restrict__ f) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double mean = sum_i[j] / (double)n;
+  f[j] = 2.0 * mean / sqrt(alpha * mean + sigma_g * sigma_g);
+}
+
+}  // namespace
+
+fkk_status launch_noise_scale(fkk_ctx* ctx, const double* sum_i, int64_t n, int m, double alpha,
+                              double sigma_g, double* f, cudaStream_t st) {
+  FKK_COUNT_LAUNCH(); noise_scale_kernel<<<(m + 127) / 128, 128, 0, st>>>(sum_i, n, m, alpha, sigma_g, f);
+  return cuda_check(ctx, cudaGetLastError(), "noise_scale launch");
+}
+
+fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double* g, cudaStream_t st) {
+  fkk_status s;
+  const int mb = L.mg / kTileM;
+  const int jbs = L.mg / kTileN;
+  int ntiles = 0;
+  for (int q = 0; q < jbs; ++q) ntiles += (2 * (q + 1) < mb ? 2 * (q + 1) : mb);
+  const int64_t nkb = L.np / kBK;
+  // enough CTAs for several waves, at least 8 K-blocks each
+  int64_t splits = ((int64_t)ctx->sm_count * 5 + ntiles - 1) / ntiles;
+  if (splits > nkb / 8) splits = nkb / 8;
+  if (splits < 1) splits = 1;
+  float* partial =
+      (float*)workspace(ctx, "gram_partial", (size_t)splits * ntiles * kTileM * kTileN * sizeof(float), &s);
+  if (!partial) return s;
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  const uint64_t row_bytes = (uint64_t)L.np * 2;
+  FKK_TRY(make_tmap_2d(ctx, &ta_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_hi, L.np, L.mg, row_bytes, kBK, kTileM,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &ta_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_lo, L.np, L.mg, row_bytes, kBK, kTileM,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tb_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_hi, L.np, L.mg, row_bytes, kBK, kTileN,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tb_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_lo, L.np, L.mg, row_bytes, kBK, kTileN,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_CUDA(ctx, cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem));
+  GramArgs a{mb, ntiles, nkb, (int)splits, partial, ctx->d_status};
+  FKK_COUNT_LAUNCH(); gram_tc_kernel<<<dim3(ntiles, (unsigned)splits), 128, kGramSmem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
+  FKK_CUDA(ctx, cudaGetLastError());
+  dim3 grid((L.m + 127) / 128, L.m);
+  FKK_COUNT_LAUNCH(); gram_assemble_kernel<<<grid, 128, 0, st>>>(partial, (int)splits, ntiles, mb, L.m, L.n, L.c, L.sum_d, f, g);
+  return cuda_check(ctx, cudaGetLastError(), "gram_assemble launch");
+}
+
+}  // namespace fkk

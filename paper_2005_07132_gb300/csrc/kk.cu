@@ -135,7 +135,7 @@ fkk_status launch_kk(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_
   int64_t grid = std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm);
   if (grid < 1) grid = 1;
   KKArgs a{i_cars, n, m, ld, i_ref, L, floor_, im, re, ld_out, ctx->d_status};
-  kk_pairs_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a, tpf);
+  FKK_COUNT_LAUNCH(); kk_pairs_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a, tpf);
   return cuda_check(ctx, cudaGetLastError(), "kk_pairs_kernel launch");
 }
 
