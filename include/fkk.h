@@ -104,6 +104,12 @@ fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on);
  * synchronises on its last event. */
 fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
 
+/* With timing on, the fp32 Jacobi sweeps of the last eigensolve record the
+ * SM clock cycles its first CTA spent per phase: 0 loading the pair block,
+ * 1 the inner sweeps, 2 re-orthonormalising the rotation, 3 row update,
+ * 4 grid barrier, 5 column update, 6 grid barrier.  Copies n (<= 8) words. */
+fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n);
+
 /* ------------------------------------------------------------------ */
 /* Conventional per-spectrum KK (Eq. KCARS with the surrogate, Eq. K)   */
 /* ------------------------------------------------------------------ */

@@ -45,6 +45,7 @@ SIGNATURES = {
     "fkk_launch_count": (C.c_uint64, []),
     "fkk_set_timing": (_I32, [_P, _I32]),
     "fkk_stage_ms": (_I32, [_P, C.POINTER(C.c_float), _I32]),
+    "fkk_eig_phase_cycles": (_I32, [_P, C.POINTER(_I64), _I32]),
     "fkk_create": (_I32, [C.POINTER(_P), _I32, _SZ]),
     "fkk_destroy": (_I32, [_P]),
     "fkk_last_error": (C.c_char_p, [_P]),
@@ -184,6 +185,11 @@ class Context:
         arr = (C.c_float * 6)()
         self.check(lib().fkk_stage_ms(self._h, arr, 6), "fkk_stage_ms")
         return dict(zip(self.STAGES, [float(v) for v in arr]))
+
+    def eig_phase_cycles(self):
+        arr = (_I64 * 8)()
+        self.check(lib().fkk_eig_phase_cycles(self._h, arr, 8), "fkk_eig_phase_cycles")
+        return list(arr)[:7]
 
     def eig_sweeps(self, stream=None):
         """(fp32 Jacobi sweeps, fp64 refinement sweeps) of the last eigensolve."""

@@ -170,4 +170,17 @@ fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n) {
   return FKK_OK;
 }
 
+fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n) {
+  if (!ctx || !cycles || n < 1) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->ws.find("eig_phase_cycles");
+  if (it == ctx->ws.end() || !it->second.ptr) return fail(ctx, FKK_ERR_INVALID_ARG, "no timed eigensolve recorded");
+  FKK_TRY(bind(ctx));
+  long long h[8];
+  FKK_CUDA(ctx, cudaDeviceSynchronize());
+  FKK_CUDA(ctx, cudaMemcpy(h, it->second.ptr, sizeof h, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n && i < 8; ++i) cycles[i] = h[i];
+  return FKK_OK;
+}
+
 }  // extern "C"

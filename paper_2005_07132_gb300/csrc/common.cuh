@@ -31,40 +31,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Grid-wide barrier for a cooperative launch with a bounded spin.  All
-// blocks must call it the same number of times.  `bar` points at two
-// unsigned words {arrived, generation} zeroed before the launch.  Returns
-// false (and records FKK_ERR_TIMEOUT) if the wait exceeded ~`limit`
-// polls, or if another block already gave up (abort flag set).
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, int* abort_flag,
-                                          long long* status, unsigned limit = (1u << 22)) {
+// Grid-wide barrier for a cooperative launch with a bounded spin: a
+// monotonic arrival counter (release on arrive, acquire on poll).  All
+// blocks call it the same number of times with their own `target`, which
+// starts at 0.  Returns false (and records FKK_ERR_TIMEOUT) if the wait
+// exceeded `limit` polls, or if another block already gave up (abort flag).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned nblocks, unsigned& target, int* abort_flag,
+                                          long long* status, unsigned limit = (1u << 21)) {
   __shared__ int ok_s;
+  target += nblocks;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned* gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned it = 0;
-      while (*gen == g) {
+    red_add_release_gpu(count, 1u);
+    unsigned it = 0;
+    while (ld_acquire_gpu(count) < target) {
+      if ((++it & 255) == 0) {
         if (*(volatile int*)abort_flag) { ok = 0; break; }
-        if (++it > limit) {
+        if (it > limit) {
           ok = 0;
           atomicExch(abort_flag, 1);
           record_error(status, kErrTimeout);
           break;
         }
-        if (it > 512) __nanosleep(32);
       }
     }
-    __threadfence();
-    if (*(volatile int*)abort_flag) ok = 0;
     ok_s = ok;
   }
   __syncthreads();

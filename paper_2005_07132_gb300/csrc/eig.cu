@@ -18,8 +18,13 @@
 // criterion); the sweep loop ends after a sweep in which no pair exceeded it.
 // Grid barriers spin a bounded number of times and report FKK_ERR_TIMEOUT.
 //
-// Refinement: Q = orth(V_K') by Cholesky-QR in fp64, H = Q^T G Q, H = W
-// diag(theta) W^T by fp64 block Jacobi, V_k = Q W[:, top k], lambda = theta.
+// Before the sweeps, the dominant eigenpair (rho, x) is found by fp64 power
+// iteration; when it has converged the sweeps run on G - rho x x^T, so their
+// fp32 rounding is relative to the second eigenvalue rather than the first.
+//
+// Refinement: Q = orth([x, V_K'-1]) by Newton-Schulz steps in fp64,
+// H = Q^T G Q with the original G, H = W diag(theta) W^T by a one-block fp64
+// Jacobi method, V_k = Q W[:, top k], lambda = theta.
 #include <algorithm>
 
 #include "common.cuh"
@@ -60,6 +65,9 @@ struct JacobiArgs {
   int* sweep_rot;
   int* sweeps_done;
   long long* status;
+  int cpp;          // CTAs per block pair (phase 2 split)
+  int inner_sweeps;
+  long long* phase_cycles;  // optional: block 0 accumulates clock64 per phase (8 words)
 };
 
 // circle schedule of the 16 indices of a block pair: kPair16[r][i] = (p, q)
@@ -86,6 +94,22 @@ __device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T& c, T& s) {
   s = t * c;
 }
 
+// fp32 rotation with fast division / reciprocal square root: the resulting
+// E is re-orthonormalised afterwards, so only the reduction of the
+// off-diagonal entry matters here.
+__device__ __forceinline__ void sym_schur2_fast(float app, float aqq, float apq, float& c, float& s) {
+  float tau = __fdividef(aqq - app, 2.f * apq);
+  float t = copysignf(1.f, tau) * __frcp_rn(fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+  c = rsqrtf(fmaf(t, t, 1.f));
+  s = t * c;
+}
+__device__ __forceinline__ void rotation(float app, float aqq, float apq, float& c, float& s) {
+  sym_schur2_fast(app, aqq, apq, c, s);
+}
+__device__ __forceinline__ void rotation(double app, double aqq, double apq, double& c, double& s) {
+  sym_schur2(app, aqq, apq, c, s);
+}
+
 template <typename T>
 __device__ __forceinline__ bool significant(T app, T aqq, T apq, T tol) {
   return fabs(apq) > tol * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > T(1e-30);
@@ -96,7 +120,7 @@ __device__ __forceinline__ bool significant(T app, T aqq, T apq, T tol) {
 // whether any pair was significant at the start (block-uniform).
 template <typename T>
 __device__ __forceinline__ bool inner_sweep(T (*S)[kJ + 1], T (*E)[kJ + 1], T* cs_c, T* cs_s, int* flag, T tol,
-                                            int tid) {
+                                            int tid, int nsweeps) {
   if (tid == 0) *flag = 0;
   {
     const int a = tid / kJ, b = tid % kJ;
@@ -109,12 +133,13 @@ __device__ __forceinline__ bool inner_sweep(T (*S)[kJ + 1], T (*E)[kJ + 1], T* c
   }
   __syncthreads();
   if (!*flag) return false;
-  for (int r = 0; r < kJ - 1; ++r) {
+  for (int rr = 0; rr < nsweeps * (kJ - 1); ++rr) {
+    const int r = rr % (kJ - 1);
     if (tid < kJ / 2) {
       const int p = kPair16[r][tid][0], q = kPair16[r][tid][1];
       T apq = S[p][q];
       T c = T(1), s = T(0);
-      if (significant(S[p][p], S[q][q], apq, tol)) sym_schur2(S[p][p], S[q][q], apq, c, s);
+      if (significant(S[p][p], S[q][q], apq, tol)) rotation(S[p][p], S[q][q], apq, c, s);
       cs_c[tid] = c;
       cs_s[tid] = s;
     }
@@ -149,22 +174,41 @@ __device__ __forceinline__ bool inner_sweep(T (*S)[kJ + 1], T (*E)[kJ + 1], T* c
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T> p) {
+  // phase clock (block 0, thread 0) when p.phase_cycles is set:
+  // 0 S load, 1 inner sweeps, 2 Newton-Schulz, 3 phase 2a, 4 barrier, 5 phase 2b, 6 barrier
+  long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long t_prev = 0;
+  const bool prof = p.phase_cycles && blockIdx.x == 0 && threadIdx.x == 0;
+#define FKK_PHASE(i)                         \
+  if (prof) {                                \
+    long long t_now = clock64();             \
+    pc[i] += t_now - t_prev;                 \
+    t_prev = t_now;                          \
+  }
   __shared__ T S[kJ][kJ + 1];
   __shared__ T E[kJ][kJ + 1];
   __shared__ T F[kJ][kJ + 1];
+  __shared__ __align__(16) T Et[kJ][kJ];  // E transposed: Et[b][a] = E[a][b]
   __shared__ T cs_c[kJ / 2], cs_s[kJ / 2];
   __shared__ int J[kJ];
   __shared__ int rot_s;
   extern __shared__ __align__(16) unsigned char stage_raw[];
-  T* stage = reinterpret_cast<T*>(stage_raw);  // kJ x mp staging (rows or columns)
+  T* stage = reinterpret_cast<T*>(stage_raw);  // kJ x (mp / cpp) staging
+  using V = typename V4<T>::type;
+  constexpr int VN = V4<T>::n;
   const int tid = threadIdx.x;
   const int mp = p.mp;
+  const int pair = blockIdx.x / p.cpp, part = blockIdx.x % p.cpp;
+  const int span = mp / p.cpp;             // columns (2a) / rows (2b) of this CTA
+  const int c0 = part * span;
+  unsigned target = 0;
   int sweep = 0;
   bool ok = true;
   for (; sweep < p.max_sweeps && ok; ++sweep) {
     for (int r = 0; r < p.nblk - 1 && ok; ++r) {
       int P, Q;
-      circle_pair(blockIdx.x, r, p.nblk, P, Q);
+      if (prof) t_prev = clock64();
+      circle_pair(pair, r, p.nblk, P, Q);
       if (tid < kJ) J[tid] = (tid < kB) ? P * kB + tid : Q * kB + (tid - kB);
       __syncthreads();
       {
@@ -174,95 +218,128 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
         S[a][b] = T(0.5) * (x + y);
       }
       __syncthreads();
-      const bool rot = inner_sweep<T>(S, E, cs_c, cs_s, &rot_s, p.tol, tid);
-      if (rot && tid == 0) atomicAdd(&p.sweep_rot[sweep], 1);
+      FKK_PHASE(0);
+      // phase 1 (every CTA of the pair computes the same E)
+      const bool rot = inner_sweep<T>(S, E, cs_c, cs_s, &rot_s, p.tol, tid, p.inner_sweeps);
+      FKK_PHASE(1);
+      if (rot && part == 0 && tid == 0) atomicAdd(&p.sweep_rot[sweep], 1);
       if (!rot) {
-        // nothing significant in this pair (E = I): keep the barrier count
-        ok = grid_sync(p.bar, gridDim.x, p.abort_flag, p.status);
-        if (ok) ok = grid_sync(p.bar, gridDim.x, p.abort_flag, p.status);
+        ok = grid_sync(p.bar, gridDim.x, target, p.abort_flag, p.status);
+        if (ok) ok = grid_sync(p.bar, gridDim.x, target, p.abort_flag, p.status);
         continue;
       }
-      if (sizeof(T) == 4) {
-        // Newton-Schulz: E <- E (3 I - E^T E) / 2
+      {
         const int a = tid / kJ, b = tid % kJ;
-        T f = T(0);
+        if (sizeof(T) == 4) {
+          // Newton-Schulz: E <- E (3 I - E^T E) / 2
+          T f = T(0);
 #pragma unroll
-        for (int q = 0; q < kJ; ++q) f += E[q][a] * E[q][b];
-        F[a][b] = f;
-        __syncthreads();
-        T e = T(0);
+          for (int q = 0; q < kJ; ++q) f += E[q][a] * E[q][b];
+          F[a][b] = f;
+          __syncthreads();
+          T e = T(0);
 #pragma unroll
-        for (int q = 0; q < kJ; ++q) e += E[a][q] * ((q == b ? T(3) : T(0)) - F[q][b]);
-        __syncthreads();
-        E[a][b] = T(0.5) * e;
-        __syncthreads();
-      }
-      // phase 2a: rows J of Gw and V^T <- E^T rows, staged through shared
-      // memory (all loads in flight, then the 16x16 transform per column)
-      for (int mat = 0; mat < 2; ++mat) {
-        T* base = mat ? p.vt : p.gw;
-        const int nv = mp / V4<T>::n;  // vectors per row
-        for (int t = tid; t < kJ * nv; t += kThreads) {
-          const int a = t / nv, cv = t % nv;
-          reinterpret_cast<typename V4<T>::type*>(stage + a * mp)[cv] =
-              reinterpret_cast<const typename V4<T>::type*>(base + (int64_t)J[a] * mp)[cv];
+          for (int q = 0; q < kJ; ++q) e += E[a][q] * ((q == b ? T(3) : T(0)) - F[q][b]);
+          Et[b][a] = T(0.5) * e;
+        } else {
+          Et[b][a] = E[a][b];
         }
         __syncthreads();
-        for (int c = tid; c < mp; c += kThreads) {
+      }
+      FKK_PHASE(2);
+      // phase 2a: rows J of Gw and V^T, columns [c0, c0 + span), <- E^T rows;
+      // both matrices staged together (rows 0..15 Gw, 16..31 V^T)
+      {
+        const int nv = span / VN;
+        for (int a = 0; a < 2 * kJ; ++a) {
+          const T* src = (a < kJ ? p.gw : p.vt) + (int64_t)J[a & (kJ - 1)] * mp + c0;
+          for (int cv = tid; cv < nv; cv += kThreads)
+            reinterpret_cast<V*>(stage + a * span)[cv] = reinterpret_cast<const V*>(src)[cv];
+        }
+        __syncthreads();
+        for (int c = tid; c < 2 * span; c += kThreads) {
+          const int mat = c >= span;
+          const int cc = c - mat * span;
+          T* col = stage + mat * kJ * span + cc;
           T g[kJ];
 #pragma unroll
-          for (int a = 0; a < kJ; ++a) g[a] = stage[a * mp + c];
-#pragma unroll
+          for (int a = 0; a < kJ; ++a) g[a] = col[a * span];
+#pragma unroll 2
           for (int b = 0; b < kJ; ++b) {
             T sg = T(0);
 #pragma unroll
-            for (int a = 0; a < kJ; ++a) sg = fma(E[a][b], g[a], sg);
-            stage[b * mp + c] = sg;
+            for (int a4 = 0; a4 < kJ; a4 += VN) {
+              V e = *reinterpret_cast<const V*>(&Et[b][a4]);
+              if constexpr (VN == 4) {
+                sg = fma(e.x, g[a4], sg);
+                sg = fma(e.y, g[a4 + 1], sg);
+                sg = fma(e.z, g[a4 + 2], sg);
+                sg = fma(e.w, g[a4 + 3], sg);
+              } else {
+                sg = fma(e.x, g[a4], sg);
+                sg = fma(e.y, g[a4 + 1], sg);
+              }
+            }
+            col[b * span] = sg;
           }
         }
         __syncthreads();
-        for (int t = tid; t < kJ * nv; t += kThreads) {
-          const int a = t / nv, cv = t % nv;
-          reinterpret_cast<typename V4<T>::type*>(base + (int64_t)J[a] * mp)[cv] =
-              reinterpret_cast<const typename V4<T>::type*>(stage + a * mp)[cv];
+        for (int a = 0; a < 2 * kJ; ++a) {
+          T* dst = (a < kJ ? p.gw : p.vt) + (int64_t)J[a & (kJ - 1)] * mp + c0;
+          for (int cv = tid; cv < nv; cv += kThreads)
+            reinterpret_cast<V*>(dst)[cv] = reinterpret_cast<const V*>(stage + a * span)[cv];
         }
-        __syncthreads();
       }
-      ok = grid_sync(p.bar, gridDim.x, p.abort_flag, p.status);
+      FKK_PHASE(3);
+      ok = grid_sync(p.bar, gridDim.x, target, p.abort_flag, p.status);
+      FKK_PHASE(4);
       if (!ok) break;
-      // phase 2b: columns J of Gw <- columns E (two 8-wide segments per row)
+      // phase 2b: rows [c0, c0 + span) of columns J of Gw <- columns E
       {
-        constexpr int vpb = kB / V4<T>::n;  // vectors per 8-wide segment
-        for (int t = tid; t < mp * 2 * vpb; t += kThreads) {
+        constexpr int vpb = kB / VN;  // vectors per 8-wide segment
+        for (int t = tid; t < span * 2 * vpb; t += kThreads) {
           const int rr = t / (2 * vpb), q = t % (2 * vpb);
           const int seg = q / vpb, v = q % vpb;
-          const int col0 = (seg ? J[kB] : J[0]) + v * V4<T>::n;
-          reinterpret_cast<typename V4<T>::type*>(stage + rr * kJ + seg * kB)[v] =
-              *reinterpret_cast<const typename V4<T>::type*>(p.gw + (int64_t)rr * mp + col0);
+          const int col0 = (seg ? J[kB] : J[0]) + v * VN;
+          reinterpret_cast<V*>(stage + rr * kJ + seg * kB)[v] =
+              *reinterpret_cast<const V*>(p.gw + (int64_t)(c0 + rr) * mp + col0);
         }
         __syncthreads();
-        for (int rr = tid; rr < mp; rr += kThreads) {
+        for (int rr = tid; rr < span; rr += kThreads) {
           T h[kJ];
 #pragma unroll
           for (int a = 0; a < kJ; ++a) h[a] = stage[rr * kJ + a];
-#pragma unroll
+#pragma unroll 2
           for (int b = 0; b < kJ; ++b) {
             T sg = T(0);
 #pragma unroll
-            for (int a = 0; a < kJ; ++a) sg = fma(h[a], E[a][b], sg);
+            for (int a4 = 0; a4 < kJ; a4 += VN) {
+              V e = *reinterpret_cast<const V*>(&Et[b][a4]);
+              if constexpr (VN == 4) {
+                sg = fma(h[a4], e.x, sg);
+                sg = fma(h[a4 + 1], e.y, sg);
+                sg = fma(h[a4 + 2], e.z, sg);
+                sg = fma(h[a4 + 3], e.w, sg);
+              } else {
+                sg = fma(h[a4], e.x, sg);
+                sg = fma(h[a4 + 1], e.y, sg);
+              }
+            }
             stage[rr * kJ + b] = sg;
           }
         }
         __syncthreads();
-        for (int t = tid; t < mp * 2 * vpb; t += kThreads) {
+        for (int t = tid; t < span * 2 * vpb; t += kThreads) {
           const int rr = t / (2 * vpb), q = t % (2 * vpb);
           const int seg = q / vpb, v = q % vpb;
-          const int col0 = (seg ? J[kB] : J[0]) + v * V4<T>::n;
-          *reinterpret_cast<typename V4<T>::type*>(p.gw + (int64_t)rr * mp + col0) =
-              reinterpret_cast<const typename V4<T>::type*>(stage + rr * kJ + seg * kB)[v];
+          const int col0 = (seg ? J[kB] : J[0]) + v * VN;
+          *reinterpret_cast<V*>(p.gw + (int64_t)(c0 + rr) * mp + col0) =
+              reinterpret_cast<const V*>(stage + rr * kJ + seg * kB)[v];
         }
       }
-      ok = grid_sync(p.bar, gridDim.x, p.abort_flag, p.status);
+      FKK_PHASE(5);
+      ok = grid_sync(p.bar, gridDim.x, target, p.abort_flag, p.status);
+      FKK_PHASE(6);
     }
     if (!ok) break;
     if (*(volatile int*)&p.sweep_rot[sweep] == 0) {
@@ -270,6 +347,9 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
       break;
     }
   }
+#undef FKK_PHASE
+  if (prof)
+    for (int i = 0; i < 8; ++i) p.phase_cycles[i] = pc[i];
   if (blockIdx.x == 0 && tid == 0) {
     *p.sweeps_done = sweep;
     if (ok && sweep >= p.max_sweeps && p.sweep_rot[p.max_sweeps - 1] != 0) record_error(p.status, kErrNotConverged);
@@ -469,6 +549,106 @@ __global__ void finish_kernel(const double* __restrict__ q, int m, int kk, const
   for (int j = threadIdx.x; j < m; j += blockDim.x) v[(int64_t)j * k + c] *= sgn;
 }
 
+__global__ void diag_start_kernel(const double* __restrict__ g, int m, double* __restrict__ x) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) x[j] = sqrt(fabs(g[(int64_t)j * m + j])) + 1e-300;
+}
+
+// y = G x (fp64, m x m row-major): one warp per row.
+__global__ void matvec64_kernel(const double* __restrict__ g, int m, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double s = 0.0;
+  for (int j = lane; j < m; j += 32) s = fma(g[(int64_t)row * m + j], x[j], s);
+  s = warp_sum(s);
+  if (lane == 0) y[row] = s;
+}
+
+// x <- y / ||y||; scal[0] = x^T y_prev-style Rayleigh quotient (y . x_old),
+// scal[1] = ||y||.  One block.
+__global__ void normalize64_kernel(double* __restrict__ x, const double* __restrict__ y, int m,
+                                   double* __restrict__ scal) {
+  __shared__ double red[2][32];
+  double ss = 0.0, rq = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    ss = fma(y[j], y[j], ss);
+    rq = fma(y[j], x[j], rq);
+  }
+  ss = warp_sum(ss);
+  rq = warp_sum(rq);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ss;
+    red[1][threadIdx.x >> 5] = rq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    red[0][0] = sqrt(a);
+    scal[0] = b;  // x^T G x for the unit x
+    scal[1] = red[0][0];
+  }
+  __syncthreads();
+  const double inv = red[0][0] > 0.0 ? 1.0 / red[0][0] : 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) x[j] = y[j] * inv;
+}
+
+// Deflation test: with the power-iteration pair (rho = x^T G x, y = G x),
+// flag[0] = 1 when ||y - rho x|| <= 1e-9 rho.  One block.
+__global__ void deflate_test_kernel(const double* __restrict__ x, const double* __restrict__ y, int m,
+                                    const double* __restrict__ scal, int* __restrict__ flag) {
+  __shared__ double red[32];
+  const double rho = scal[0];
+  double r2 = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double d = y[j] - rho * x[j];
+    r2 = fma(d, d, r2);
+  }
+  r2 = warp_sum(r2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    flag[0] = (rho > 0.0 && sqrt(t) <= 1e-9 * rho) ? 1 : 0;
+  }
+}
+
+// Gd = G - rho x x^T when flag[0], else Gd = G.  grid = (cols, m).
+__global__ void deflate64_kernel(const double* __restrict__ g, int m, const double* __restrict__ x,
+                                 const double* __restrict__ scal, const int* __restrict__ flag,
+                                 double* __restrict__ gd) {
+  const int r = blockIdx.y;
+  const int use = flag[0];
+  const double rho = scal[0];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    double v = g[(int64_t)r * m + c];
+    if (use) v -= rho * x[r] * x[c];
+    gd[(int64_t)r * m + c] = v;
+  }
+}
+
+// Leading refinement basis: column 0 = x (when deflated), then the largest
+// Jacobi vectors of the deflated matrix.  X[j, c] row-major m x kk.
+template <typename T>
+__global__ void gather_defl_kernel(const T* __restrict__ vt, int m, int mp, const int* __restrict__ order, int kk,
+                                   const double* __restrict__ x, const int* __restrict__ flag,
+                                   double* __restrict__ out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (j >= m) return;
+  const int use = flag[0];
+  double v;
+  if (use && c == 0) v = x[j];
+  else v = (double)vt[(int64_t)order[use ? c - 1 : c] * mp + j];
+  out[(int64_t)j * kk + c] = v;
+}
+
 template <typename T>
 fkk_status run_block_jacobi(fkk_ctx* ctx, const char* tag, const double* g, int m, int ldg, T tol, int max_sweeps,
                             T** gw_out, T** vt_out, int* mp_out, int diag_word, cudaStream_t st) {
@@ -493,16 +673,24 @@ fkk_status run_block_jacobi(fkk_ctx* ctx, const char* tag, const double* g, int 
   FKK_CUDA(ctx, cudaMemsetAsync(scr, 0, 64 + 4 * max_sweeps, st));
   FKK_COUNT_LAUNCH(); jacobi_init_kernel<T><<<dim3((mp + 255) / 256, mp), 256, 0, st>>>(g, m, ldg, mp, gw, vt);
   FKK_CUDA(ctx, cudaGetLastError());
-  const size_t stage_bytes = (size_t)kJ * mp * sizeof(T);
+  int cpp = 1;
+  while (cpp < 4 && (int64_t)npairs * cpp * 2 <= ctx->sm_count && (mp / (cpp * 2)) % V4<T>::n == 0) cpp *= 2;
+  const size_t stage_bytes = (size_t)2 * kJ * (mp / cpp) * sizeof(T);
   FKK_CUDA(ctx, cudaFuncSetAttribute(block_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes));
   int per_sm = 0;
   FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T>, kThreads, stage_bytes));
-  if ((int64_t)per_sm * ctx->sm_count < npairs)
+  if ((int64_t)per_sm * ctx->sm_count < (int64_t)npairs * cpp)
     return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: %d block pairs exceed co-resident capacity", npairs);
-  JacobiArgs<T> a{gw, vt, mp, nblk, tol, max_sweeps, bar, abort_flag, sweep_rot, sweeps_done, ctx->d_status};
+  long long* pcyc = nullptr;
+  if (ctx->timing) {
+    pcyc = (long long*)workspace(ctx, "eig_phase_cycles", 8 * sizeof(long long), &s);
+    if (!pcyc) return s;
+  }
+  JacobiArgs<T> a{gw, vt, mp, nblk, tol, max_sweeps, bar, abort_flag, sweep_rot, sweeps_done, ctx->d_status,
+                  cpp, 1, pcyc};
   void* args[] = {&a};
   FKK_COUNT_LAUNCH();
-  FKK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)block_jacobi_kernel<T>, dim3(npairs), dim3(kThreads), args,
+  FKK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)block_jacobi_kernel<T>, dim3(npairs * cpp), dim3(kThreads), args,
                                             stage_bytes, st));
   // sweep count of this solve -> status word diag_word (diagnostic)
   FKK_CUDA(ctx, cudaMemcpyAsync(ctx->d_status + diag_word, sweeps_done, sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -537,11 +725,35 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
     FKK_CUDA(ctx, cudaMemcpyToSymbol(kPair16, t, sizeof t));
     tables = true;
   }
-  // 1. fp32 block Jacobi over the whole matrix
+  // 0. dominant eigenpair by fp64 power iteration; when it has converged
+  //    (residual <= 1e-9 rho) the fp32 Jacobi works on G - rho x x^T, whose
+  //    norm is the second eigenvalue, so its rounding is relative to that
+  double* pw = (double*)workspace(ctx, "eig_pw", (size_t)(2 * m + 8) * 8, &s);
+  if (!pw) return s;
+  double* px = pw;
+  double* py = pw + m;
+  double* scal = pw + 2 * m;
+  int* flag = (int*)workspace(ctx, "eig_flag", 64, &s);
+  if (!flag) return s;
+  double* gd = (double*)workspace(ctx, "eig_gd", (size_t)m * m * 8, &s);
+  if (!gd) return s;
+  {
+    // start from the diagonal (all positive for a Gram matrix)
+    FKK_COUNT_LAUNCH(); diag_start_kernel<<<(m + 255) / 256, 256, 0, st>>>(g, m, px);
+    for (int it = 0; it < 60; ++it) {
+      FKK_COUNT_LAUNCH(); matvec64_kernel<<<(m + 7) / 8, 256, 0, st>>>(g, m, px, py);
+      FKK_COUNT_LAUNCH(); normalize64_kernel<<<1, 1024, 0, st>>>(px, py, m, scal);
+    }
+    FKK_COUNT_LAUNCH(); matvec64_kernel<<<(m + 7) / 8, 256, 0, st>>>(g, m, px, py);
+    FKK_COUNT_LAUNCH(); deflate_test_kernel<<<1, 1024, 0, st>>>(px, py, m, scal, flag);
+    FKK_COUNT_LAUNCH(); deflate64_kernel<<<dim3((m + 255) / 256, m), 256, 0, st>>>(g, m, px, scal, flag, gd);
+    FKK_CUDA(ctx, cudaGetLastError());
+  }
+  // 1. fp32 block Jacobi over the whole (deflated) matrix
   float* gw;
   float* vt;
   int mp;
-  FKK_TRY(run_block_jacobi<float>(ctx, "eig32", g, m, m, (float)(tol32 > 0 ? tol32 : 1e-6),
+  FKK_TRY(run_block_jacobi<float>(ctx, "eig32", gd, m, m, (float)(tol32 > 0 ? tol32 : 1e-6),
                                           max_sweeps32 > 0 ? max_sweeps32 : 40, &gw, &vt, &mp, 2, st));
   if (sweeps_out) FKK_CUDA(ctx, cudaMemcpyAsync(sweeps_out, ctx->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   // 2. leading K' vectors, orthonormalised in fp64 (two Newton-Schulz steps)
@@ -560,7 +772,8 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   double* ww = (double*)workspace(ctx, "eig_ww", (size_t)nsm * nsm * 8, &s);
   if (!ww) return s;
   FKK_COUNT_LAUNCH(); rank_kernel<float><<<(m + 127) / 128, 128, 0, st>>>(gw, m, mp, order, kk);
-  FKK_COUNT_LAUNCH(); gather_vecs_kernel<float><<<dim3((m + 127) / 128, kk), 128, 0, st>>>(vt, m, mp, order, kk, q);
+  FKK_COUNT_LAUNCH(); gather_defl_kernel<float><<<dim3((m + 127) / 128, kk), 128, 0, st>>>(vt, m, mp, order, kk, px,
+                                                                                            flag, q);
   for (int pass = 0; pass < 2; ++pass) {
     gemm64(q, kk, 1, q, kk, 0, h, kk, kk, kk, m, st);
     FKK_COUNT_LAUNCH(); ns_apply_kernel<<<m, 128, kk * sizeof(double), st>>>(q, m, kk, h);

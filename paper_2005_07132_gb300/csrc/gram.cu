@@ -1,8 +1,11 @@
 // Gram matrix of the transformed cube on the 5th-generation tensor cores.
 //
 // G_d = D^T D over all spectra, D = hi + lo (two bf16 terms), computed as
-// hi.hi + hi.lo + lo.hi with fp32 accumulation in TMEM (relative error of a
-// product about 2^-17; the lo.lo term is below that).  Output tiles are
+// hi.hi + hi.lo + lo.hi + lo.lo with fp32 accumulation in TMEM: every
+// product of two bf16 values is exact in fp32, so the only error left is
+// the rounding of d to hi + lo (2^-18 |d|, unbiased) and the fp32
+// accumulation (kept short by the split-K).  Dropping lo.lo would leave a
+// systematic positive bias of ~2^-18 sum d^2 on the diagonal.  Output tiles are
 // 128 (rows i) x 256 (columns j) covering the upper triangle (i-block 128*ib
 // < 256*(jb+1)); the contraction over spectra is split into `splits`
 // contiguous ranges, one CTA per (tile, split), and the fp32 partial tiles
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(128, 1)
                      (i > 0 || kk > 0) ? 1u : 0u);
         tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_hi + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
         tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_hi + off), idesc, 1u);
+        tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
       }
       tc::mma_commit(&empty[s]);
     }
@@ -235,8 +239,10 @@ fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double*
   int ntiles = 0;
   for (int q = 0; q < jbs; ++q) ntiles += (2 * (q + 1) < mb ? 2 * (q + 1) : mb);
   const int64_t nkb = L.np / kBK;
-  // enough CTAs for several waves, at least 8 K-blocks each
+  // enough CTAs for several waves, at least 8 and at most 96 K-blocks each
+  // (the fp32 TMEM accumulation length per partial tile)
   int64_t splits = ((int64_t)ctx->sm_count * 5 + ntiles - 1) / ntiles;
+  if (splits < (nkb + 95) / 96) splits = (nkb + 95) / 96;
   if (splits > nkb / 8) splits = nkb / 8;
   if (splits < 1) splits = 1;
   float* partial =
