@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
   __shared__ T S[kJ][kJ + 1];
   __shared__ T E[kJ][kJ + 1];
   __shared__ T F[kJ][kJ + 1];
-  __shared__ __align__(16) T Et[kJ][kJ];  // E transposed: Et[b][a] = E[a][b]
+  __shared__ __align__(16) T Ev[kJ][kJ];  // the (re-orthonormalised) rotation, row-major
   __shared__ T cs_c[kJ / 2], cs_s[kJ / 2];
   __shared__ int J[kJ];
   __shared__ int rot_s;
@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
           T e = T(0);
 #pragma unroll
           for (int q = 0; q < kJ; ++q) e += E[a][q] * ((q == b ? T(3) : T(0)) - F[q][b]);
-          Et[b][a] = T(0.5) * e;
+          Ev[a][b] = T(0.5) * e;
         } else {
-          Et[b][a] = E[a][b];
+          Ev[a][b] = E[a][b];
         }
         __syncthreads();
       }
@@ -251,37 +251,52 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
       // both matrices staged together (rows 0..15 Gw, 16..31 V^T)
       {
         const int nv = span / VN;
-        for (int a = 0; a < 2 * kJ; ++a) {
-          const T* src = (a < kJ ? p.gw : p.vt) + (int64_t)J[a & (kJ - 1)] * mp + c0;
-          for (int cv = tid; cv < nv; cv += kThreads)
-            reinterpret_cast<V*>(stage + a * span)[cv] = reinterpret_cast<const V*>(src)[cv];
+        const int total = 2 * kJ * nv;
+        // all of a thread's loads are issued before any shared-memory store
+        for (int base = 0; base < total; base += kThreads * 8) {
+          V r8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + tid;
+            if (idx < total) {
+              const int a = idx / nv, cv = idx - a * nv;
+              r8[u] = reinterpret_cast<const V*>((a < kJ ? p.gw : p.vt) + (int64_t)J[a & (kJ - 1)] * mp + c0)[cv];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + tid;
+            if (idx < total) reinterpret_cast<V*>(stage)[idx] = r8[u];
+          }
         }
         __syncthreads();
         for (int c = tid; c < 2 * span; c += kThreads) {
           const int mat = c >= span;
           const int cc = c - mat * span;
           T* col = stage + mat * kJ * span + cc;
-          T g[kJ];
+          asm volatile("" ::: "memory");  // keep the rotation reads inside the loop (no hoisting to registers)
+          T acc[kJ];
 #pragma unroll
-          for (int a = 0; a < kJ; ++a) g[a] = col[a * span];
-#pragma unroll 2
-          for (int b = 0; b < kJ; ++b) {
-            T sg = T(0);
+          for (int b = 0; b < kJ; ++b) acc[b] = T(0);
 #pragma unroll
-            for (int a4 = 0; a4 < kJ; a4 += VN) {
-              V e = *reinterpret_cast<const V*>(&Et[b][a4]);
+          for (int a = 0; a < kJ; ++a) {
+            const T ga = col[a * span];
+#pragma unroll
+            for (int b4 = 0; b4 < kJ; b4 += VN) {
+              V e = *reinterpret_cast<const V*>(&Ev[a][b4]);
               if constexpr (VN == 4) {
-                sg = fma(e.x, g[a4], sg);
-                sg = fma(e.y, g[a4 + 1], sg);
-                sg = fma(e.z, g[a4 + 2], sg);
-                sg = fma(e.w, g[a4 + 3], sg);
+                acc[b4] = fma(e.x, ga, acc[b4]);
+                acc[b4 + 1] = fma(e.y, ga, acc[b4 + 1]);
+                acc[b4 + 2] = fma(e.z, ga, acc[b4 + 2]);
+                acc[b4 + 3] = fma(e.w, ga, acc[b4 + 3]);
               } else {
-                sg = fma(e.x, g[a4], sg);
-                sg = fma(e.y, g[a4 + 1], sg);
+                acc[b4] = fma(e.x, ga, acc[b4]);
+                acc[b4 + 1] = fma(e.y, ga, acc[b4 + 1]);
               }
             }
-            col[b * span] = sg;
           }
+#pragma unroll
+          for (int b = 0; b < kJ; ++b) col[b * span] = acc[b];
         }
         __syncthreads();
         for (int a = 0; a < 2 * kJ; ++a) {
@@ -297,36 +312,55 @@ __global__ void __launch_bounds__(kThreads, 1) block_jacobi_kernel(JacobiArgs<T>
       // phase 2b: rows [c0, c0 + span) of columns J of Gw <- columns E
       {
         constexpr int vpb = kB / VN;  // vectors per 8-wide segment
-        for (int t = tid; t < span * 2 * vpb; t += kThreads) {
-          const int rr = t / (2 * vpb), q = t % (2 * vpb);
-          const int seg = q / vpb, v = q % vpb;
-          const int col0 = (seg ? J[kB] : J[0]) + v * VN;
-          reinterpret_cast<V*>(stage + rr * kJ + seg * kB)[v] =
-              *reinterpret_cast<const V*>(p.gw + (int64_t)(c0 + rr) * mp + col0);
+        const int total = span * 2 * vpb;
+        for (int base = 0; base < total; base += kThreads * 8) {
+          V r8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int t = base + u * kThreads + tid;
+            if (t < total) {
+              const int rr = t / (2 * vpb), q = t % (2 * vpb);
+              const int seg = q / vpb, v = q % vpb;
+              const int col0 = (seg ? J[kB] : J[0]) + v * VN;
+              r8[u] = *reinterpret_cast<const V*>(p.gw + (int64_t)(c0 + rr) * mp + col0);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int t = base + u * kThreads + tid;
+            if (t < total) {
+              const int rr = t / (2 * vpb), q = t % (2 * vpb);
+              const int seg = q / vpb, v = q % vpb;
+              reinterpret_cast<V*>(stage + rr * kJ + seg * kB)[v] = r8[u];
+            }
+          }
         }
         __syncthreads();
         for (int rr = tid; rr < span; rr += kThreads) {
-          T h[kJ];
+          T* row = stage + rr * kJ;
+          asm volatile("" ::: "memory");
+          T acc[kJ];
 #pragma unroll
-          for (int a = 0; a < kJ; ++a) h[a] = stage[rr * kJ + a];
-#pragma unroll 2
-          for (int b = 0; b < kJ; ++b) {
-            T sg = T(0);
+          for (int b = 0; b < kJ; ++b) acc[b] = T(0);
 #pragma unroll
-            for (int a4 = 0; a4 < kJ; a4 += VN) {
-              V e = *reinterpret_cast<const V*>(&Et[b][a4]);
+          for (int a = 0; a < kJ; ++a) {
+            const T ha = row[a];
+#pragma unroll
+            for (int b4 = 0; b4 < kJ; b4 += VN) {
+              V e = *reinterpret_cast<const V*>(&Ev[a][b4]);
               if constexpr (VN == 4) {
-                sg = fma(h[a4], e.x, sg);
-                sg = fma(h[a4 + 1], e.y, sg);
-                sg = fma(h[a4 + 2], e.z, sg);
-                sg = fma(h[a4 + 3], e.w, sg);
+                acc[b4] = fma(ha, e.x, acc[b4]);
+                acc[b4 + 1] = fma(ha, e.y, acc[b4 + 1]);
+                acc[b4 + 2] = fma(ha, e.z, acc[b4 + 2]);
+                acc[b4 + 3] = fma(ha, e.w, acc[b4 + 3]);
               } else {
-                sg = fma(h[a4], e.x, sg);
-                sg = fma(h[a4 + 1], e.y, sg);
+                acc[b4] = fma(ha, e.x, acc[b4]);
+                acc[b4 + 1] = fma(ha, e.y, acc[b4 + 1]);
               }
             }
-            stage[rr * kJ + b] = sg;
           }
+#pragma unroll
+          for (int b = 0; b < kJ; ++b) row[b] = acc[b];
         }
         __syncthreads();
         for (int t = tid; t < span * 2 * vpb; t += kThreads) {

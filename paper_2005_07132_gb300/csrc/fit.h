@@ -100,6 +100,10 @@ fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmi
 fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
                               const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
 
+// Same, on the tensor cores (bf16 x3 operands, exp / sin epilogue), k <= 128.
+fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                                 const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
+
 // Tensor map helper (driver entry point fetched once).
 fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,
                         uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,

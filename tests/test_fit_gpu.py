@@ -152,6 +152,26 @@ def test_basis_math(fk, ctx, cube1, pec, sec_mode):
     assert rel_l2(cp.cpu().numpy(), out[6]) <= 1e-9
 
 
+@pytest.mark.parametrize("n,k,m,ld_pad", [(1000, 80, 300, 0), (129, 13, 877, 3), (5000, 64, 512, 0), (1, 1, 8, 0)])
+def test_reconstruct_shapes(fk, ctx, n, k, m, ld_pad):
+    """Tensor-core reconstruction: K padded to 64 / 128, ragged rows and
+    channels, row stride above M, Im and Re."""
+    r = np.random.default_rng(n + k + m)
+    P = (r.standard_normal((n, k)) * 0.05).astype(np.float32)
+    ca = r.standard_normal((k, m)) * 0.5
+    cp = r.standard_normal((k, m)) * 0.5
+    re_o, im_o = O.reconstruct(P.astype(np.float64), ca, cp)
+    ld = m + ld_pad
+    im_buf = torch.full((n, ld), 9.0, device="cuda")
+    re_buf = torch.full((n, ld), 9.0, device="cuda")
+    fk.fkk_reconstruct(ctx, _dev(P), _dev(ca), _dev(cp), im_out=im_buf[:, :m], re_out=re_buf[:, :m])
+    im = im_buf.cpu().numpy()
+    re = re_buf.cpu().numpy()
+    assert rel_l2(im[:, :m], im_o) <= 1e-5
+    assert rel_l2(re[:, :m], re_o) <= 1e-5
+    assert np.all(im[:, m:] == 9.0) and np.all(re[:, m:] == 9.0)
+
+
 def test_reconstruct(fk, ctx, cube1):
     A = O.log_ratio(cube1.i_cars, cube1.i_ref)
     b, P_o, _ = O.fit(cube1.i_cars, cube1.i_ref, O.FitParams(k=20))
