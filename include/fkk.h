@@ -268,6 +268,43 @@ fkk_status fkk_reconstruct(fkk_ctx* ctx, const float* p, int64_t n_spectra, int3
                            const double* c_amp, const double* c_ph, float* im_out, float* re_out, int64_t ld_out,
                            void* stream);
 
+/* Largest problem fkk_reconstruct_noalloc accepts in one call. */
+#define FKK_NOALLOC_MAX_SPECTRA 16384
+#define FKK_NOALLOC_MAX_CHANNELS 2048
+
+/* fkk_reconstruct_noalloc: the same reconstruction as fkk_reconstruct
+ * (Eq. fKKEC; same kernels, same arguments and layout, identical results),
+ * but it allocates no device memory.  The paper has no counterpart: this is
+ * an interface of this library for callers that cannot allocate, e.g. a
+ * serving loop that has fixed its HBM footprint at start-up, or code that
+ * must not hit the implicit device synchronisation of cudaMalloc/cudaFree.
+ * fkk_reconstruct keeps its packed operands in the context's grow-only
+ * workspace, which is (re)allocated the first time a larger batch arrives;
+ * this entry point packs them instead into two fixed arrays compiled into
+ * the library (10 MiB of static device memory per device: bf16 hi/lo
+ * copies of P for up to FKK_NOALLOC_MAX_SPECTRA rows at K = 128, and of the
+ * interleaved coefficients for up to FKK_NOALLOC_MAX_CHANNELS channels).
+ *
+ * Limits: 0 <= n_spectra <= FKK_NOALLOC_MAX_SPECTRA, 1 <= k <= 80,
+ * 1 <= m <= FKK_NOALLOC_MAX_CHANNELS, ld_out >= m; anything larger returns
+ * FKK_ERR_INVALID_ARG with a message in fkk_last_error() and launches
+ * nothing (split larger batches into calls of at most the maximum).
+ * Setup: the first call on a device looks up the addresses of the static
+ * arrays (cudaGetSymbolAddress, which may load the library's device code on
+ * that device); make that first call before any stream capture.  A call
+ * with n_spectra == 0 does only this setup and accepts NULL data pointers.
+ * Nothing in the arrays needs to start at zero: every call rewrites the
+ * whole region its kernels read (zero padding included).
+ * Concurrency: the arrays are shared by every context of the process on
+ * that device, so calls whose work overlaps on the device (other streams,
+ * other threads or contexts) race on them and give wrong results; order
+ * such calls on one stream or with events.  Device-side errors are reported
+ * through fkk_sync_status() of ctx as for the other calls.
+ * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_CUDA. */
+fkk_status fkk_reconstruct_noalloc(fkk_ctx* ctx, const float* p, int64_t n_spectra, int32_t k, int32_t m,
+                                   const double* c_amp, const double* c_ph, float* im_out, float* re_out,
+                                   int64_t ld_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ SIGNATURES = {
     "fkk_project": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_basis_math": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_reconstruct": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
+    "fkk_reconstruct_noalloc": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
 }
 
 
@@ -390,4 +391,24 @@ def fkk_reconstruct(ctx: Context, p, c_amp, c_ph, im_out=None, re_out=None, stre
     st = lib().fkk_reconstruct(ctx.handle, _ptr(p), n, k, m, _ptr(c_amp), _ptr(c_ph), _ptr(im_out), _ptr(re_out),
                                im_out.stride(0), _stream(stream))
     ctx.check(st, "fkk_reconstruct")
+    return (im_out, re_out) if re_out is not None else im_out
+
+
+def fkk_reconstruct_noalloc(ctx: Context, p, c_amp, c_ph, im_out, re_out=None, stream=None):
+    """Same as fkk_reconstruct, through the entry point that allocates no
+    device memory (fixed scratch inside the library; at most
+    FKK_NOALLOC_MAX_SPECTRA rows and FKK_NOALLOC_MAX_CHANNELS channels per
+    call).  The outputs must be supplied.  p may be None with zero rows: that
+    call only performs the per-device setup."""
+    if p is None:
+        st = lib().fkk_reconstruct_noalloc(ctx.handle, None, 0, 1, 1, None, None, None, None, 1, _stream(stream))
+        ctx.check(st, "fkk_reconstruct_noalloc")
+        return im_out
+    for t, nm in ((p, "p"), (c_amp, "c_amp"), (c_ph, "c_ph")):
+        _dense(t, nm)
+    n, k = p.shape
+    m = c_amp.shape[1]
+    st = lib().fkk_reconstruct_noalloc(ctx.handle, _ptr(p), n, k, m, _ptr(c_amp), _ptr(c_ph), _ptr(im_out),
+                                       _ptr(re_out), im_out.stride(0), _stream(stream))
+    ctx.check(st, "fkk_reconstruct_noalloc")
     return (im_out, re_out) if re_out is not None else im_out

@@ -104,6 +104,15 @@ fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, in
 fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
                                  const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
 
+// Same, with the packed operands in caller-provided scratch instead of the
+// context's workspace: p_hi / p_lo hold ceil(n / 128) * 128 x Kp bf16 each,
+// c_hi / c_lo ceil(2m / 256) * 256 x Kp bf16 each (Kp = 64 for k <= 64,
+// else 128), each 16-byte aligned.  Allocates nothing.
+fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n, int k, int m,
+                                         const double* c_amp, const double* c_ph, float* im, float* re,
+                                         int64_t ld_out, cudaStream_t st, void* p_hi, void* p_lo, void* c_hi,
+                                         void* c_lo);
+
 // Tensor map helper (driver entry point fetched once).
 fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,
                         uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,

@@ -295,4 +295,43 @@ fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k,
   return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
 }
 
+fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n, int k, int m,
+                                         const double* c_amp, const double* c_ph, float* im, float* re,
+                                         int64_t ld_out, cudaStream_t st, void* p_hi, void* p_lo, void* c_hi,
+                                         void* c_lo) {
+  if (k > 128) return fail(ctx, FKK_ERR_INVALID_ARG, "k > 128");
+  const int kp = k <= 64 ? 64 : 128;
+  const int64_t n_pad = ((n + kTM - 1) / kTM) * kTM;
+  const int rows_c = ((2 * m + kTN - 1) / kTN) * kTN;
+  __nv_bfloat16* phi = static_cast<__nv_bfloat16*>(p_hi);
+  __nv_bfloat16* plo = static_cast<__nv_bfloat16*>(p_lo);
+  __nv_bfloat16* chi = static_cast<__nv_bfloat16*>(c_hi);
+  __nv_bfloat16* clo = static_cast<__nv_bfloat16*>(c_lo);
+  {
+    const int64_t tot = n_pad * kp;
+    FKK_COUNT_LAUNCH();
+    pack_p_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p, n, k, n_pad, kp, phi, plo);
+    const int64_t totc = (int64_t)rows_c * kp;
+    FKK_COUNT_LAUNCH();
+    pack_c_kernel<<<(unsigned)((totc + 255) / 256), 256, 0, st>>>(c_amp, c_ph, k, m, rows_c, kp, chi, clo);
+    FKK_CUDA(ctx, cudaGetLastError());
+  }
+  CUtensorMap tph, tpl, tch, tcl;
+  const uint64_t rb = (uint64_t)kp * 2;
+  FKK_TRY(make_tmap_2d(ctx, &tph, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, phi, kp, n_pad, rb, 64, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tpl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, plo, kp, n_pad, rb, 64, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, chi, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tcl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, clo, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
+  int nst = 2;
+  if (recon_smem(kp, nst) > 227 * 1024) nst = 1;
+  const size_t smem = recon_smem(kp, nst);
+  if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "reconstruction tile does not fit shared memory");
+  FKK_CUDA(ctx, cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ReconArgs a{n, m, kp, (int)(n_pad / kTM), rows_c / kTN, nst, im, re, ld_out, ctx->d_status};
+  const int grid = (int)std::min<int64_t>(ctx->sm_count, a.n_row_tiles);
+  FKK_COUNT_LAUNCH();
+  recon_tc_kernel<<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
+  return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
+}
+
 }  // namespace fkk
