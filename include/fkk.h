@@ -87,12 +87,6 @@ size_t fkk_workspace_bytes(const fkk_ctx* ctx);
  * FKK_ERR_NOT_CONVERGED), else FKK_OK.  `clamped` may be NULL. */
 fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped);
 
-/* Synchronise `stream` and read (without clearing) the sweep counts of the
- * last eigensolve: *sweeps32 of the fp32 block Jacobi over the Gram matrix,
- * *sweeps64 of the fp64 Jacobi of its Rayleigh-Ritz refinement.  Either
- * pointer may be NULL. */
-fkk_status fkk_eig_sweeps(fkk_ctx* ctx, void* stream, int32_t* sweeps32, int32_t* sweeps64);
-
 /* Turn per-stage timing of fkk_fit_basis on (1) or off (0).  When on, each
  * fit records CUDA events on its stream at the boundaries of six stages:
  * 0 transform (log ratio, split, channel sums), 1 Gram, 2 eigensolve,
@@ -104,10 +98,11 @@ fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on);
  * synchronises on its last event. */
 fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
 
-/* With timing on, the fp32 Jacobi sweeps of the last eigensolve record the
- * SM clock cycles its first CTA spent per phase: 0 loading the pair block,
- * 1 the inner sweeps, 2 re-orthonormalising the rotation, 3 row update,
- * 4 grid barrier, 5 column update, 6 grid barrier.  Copies n (<= 8) words. */
+/* With timing on, the tridiagonal reduction of the last eigensolve records
+ * the SM clock cycles its first CTA spent per phase, summed over the
+ * columns: 0 loading and scaling G, 1 the vector w, 2 the pivot column and
+ * the next reflector, 3 the update of the owned columns, 4 grid barriers.
+ * Copies n (<= 8) words. */
 fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n);
 
 /* ------------------------------------------------------------------ */
@@ -158,14 +153,11 @@ typedef struct {
   float ratio_floor;    /* I/I_ref is clamped to >= ratio_floor before the log (> 0) */
   double noise_alpha;   /* Poisson multiplier alpha of f(w) (Sec. 2.2); used when f is NULL */
   double noise_sigma_g; /* Gaussian sigma_g of f(w); alpha = sigma_g = 0 means f = 1 */
-  double eig_tol;       /* relative off-diagonal tolerance of the fp32 Jacobi sweeps; 0 = 1e-6 */
-  int32_t eig_max_sweeps; /* cap on the fp32 Jacobi sweeps; 0 = 40 */
 } fkk_fit_params;
 
 /* Defaults: k 20, pad_len 0, pec 1, sec 1, als_lambda 0 (auto), als_p 0.01,
  * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
- * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
- * eig_tol 0 (1e-6), eig_max_sweeps 0 (40). */
+ * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0. */
 void fkk_fit_params_default(fkk_fit_params* p);
 
 /* Trained artefacts (Sec. 2.6: f, S, V, Phi_PEC, V_SEC) resident on the
@@ -242,11 +234,14 @@ fkk_status fkk_gram(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_
 
 /* Top-k eigenpairs of the symmetric fp64 G (device, m x m): lam_out (k,
  * descending), v_out (m x k row-major), each column's largest-magnitude
- * entry positive.  m in [2, 2048], 1 <= k <= min(80, m).  tol: relative
- * tolerance of the fp32 Jacobi sweeps (0 = 1e-6); max_sweeps caps them
- * (0 = 40); the fp64 refinement of the leading k + 32 vectors follows. */
-fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double tol, int32_t max_sweeps,
-                        double* lam_out, double* v_out, void* stream);
+ * entry positive.  m in [2, 2048], 1 <= k <= min(80, m).  Householder
+ * tridiagonalisation, Sturm multisection and twisted-factorisation
+ * eigenvectors in double-word (about 48-bit) arithmetic; eigenvalues and
+ * residuals accurate to about 1e-13 of the largest eigenvalue.  Errors:
+ * FKK_ERR_INVALID_ARG, FKK_ERR_CUDA; a numerical breakdown (non-finite
+ * input) is reported by fkk_sync_status as FKK_ERR_NOT_CONVERGED. */
+fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double* lam_out, double* v_out,
+                        void* stream);
 
 /* P = A W (n x k fp32, row-major, device) for A as in fkk_gram and W
  * (device, m x k doubles), through the same transformed-cube path as the

@@ -51,7 +51,6 @@ SIGNATURES = {
     "fkk_last_error": (C.c_char_p, [_P]),
     "fkk_workspace_bytes": (_SZ, [_P]),
     "fkk_sync_status": (_I32, [_P, _P, C.POINTER(_I64)]),
-    "fkk_eig_sweeps": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "kk_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _I32, _F32, _P, _P, _I64, _P]),
     "fkk_fit_params_default": (None, [_P]),
     "fkk_fit_params_size": (_SZ, []),
@@ -62,7 +61,7 @@ SIGNATURES = {
     "fkk_basis_get": (_I32, [_P, _I32, _P, _SZ]),
     "fkk_basis_from_arrays": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, C.POINTER(_P)]),
     "fkk_gram": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _P]),
-    "fkk_eig_topk": (_I32, [_P, _P, _I32, _I32, _F64, _I32, _P, _P, _P]),
+    "fkk_eig_topk": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "fkk_project": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_basis_math": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_reconstruct": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
@@ -79,7 +78,6 @@ class FitParams(C.Structure):
         ("ridge_rel", C.c_double), ("sec_mode", C.c_int32), ("sg_window", C.c_int32),
         ("sg_order", C.c_int32), ("ml_lambda", C.c_double), ("precision", C.c_int32),
         ("ratio_floor", C.c_float), ("noise_alpha", C.c_double), ("noise_sigma_g", C.c_double),
-        ("eig_tol", C.c_double), ("eig_max_sweeps", C.c_int32),
     ]
 
 
@@ -188,15 +186,11 @@ class Context:
         return dict(zip(self.STAGES, [float(v) for v in arr]))
 
     def eig_phase_cycles(self):
+        """SM cycles per phase of the last timed tridiagonal reduction: load,
+        w, pivot column + reflector, column update, grid barriers."""
         arr = (_I64 * 8)()
         self.check(lib().fkk_eig_phase_cycles(self._h, arr, 8), "fkk_eig_phase_cycles")
-        return list(arr)[:7]
-
-    def eig_sweeps(self, stream=None):
-        """(fp32 Jacobi sweeps, fp64 refinement sweeps) of the last eigensolve."""
-        a, b = _I32(0), _I32(0)
-        self.check(lib().fkk_eig_sweeps(self._h, _stream(stream), C.byref(a), C.byref(b)), "fkk_eig_sweeps")
-        return a.value, b.value
+        return list(arr)[:5]
 
     def close(self):
         if self._h:
@@ -334,14 +328,14 @@ def fkk_gram(ctx: Context, i_cars, i_ref, ratio_floor: float = 1e-6, f=None, g_o
     return g_out
 
 
-def fkk_eig_topk(ctx: Context, g, k: int, tol: float = 0.0, max_sweeps: int = 0, stream=None):
+def fkk_eig_topk(ctx: Context, g, k: int, stream=None):
     import torch
 
     _dense(g, "g")
     m = g.shape[0]
     lam = torch.empty(k, dtype=torch.float64, device=g.device)
     v = torch.empty((m, k), dtype=torch.float64, device=g.device)
-    st = lib().fkk_eig_topk(ctx.handle, _ptr(g), m, k, tol, max_sweeps, _ptr(lam), _ptr(v), _stream(stream))
+    st = lib().fkk_eig_topk(ctx.handle, _ptr(g), m, k, _ptr(lam), _ptr(v), _stream(stream))
     ctx.check(st, "fkk_eig_topk")
     return lam, v
 

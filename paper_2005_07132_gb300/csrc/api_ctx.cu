@@ -139,18 +139,6 @@ fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped) {
   return static_cast<fkk_status>(h[0]);
 }
 
-fkk_status fkk_eig_sweeps(fkk_ctx* ctx, void* stream, int32_t* s32, int32_t* s64) {
-  if (!ctx) return FKK_ERR_INVALID_ARG;
-  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  FKK_TRY(bind(ctx));
-  long long h[kStatusWords];
-  FKK_CUDA(ctx, cudaStreamSynchronize(as_stream(stream)));
-  FKK_CUDA(ctx, cudaMemcpy(h, ctx->d_status, sizeof h, cudaMemcpyDeviceToHost));
-  if (s32) *s32 = (int32_t)(h[2] & 0xffffffff);
-  if (s64) *s64 = (int32_t)(h[3] & 0xffffffff);
-  return FKK_OK;
-}
-
 fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);

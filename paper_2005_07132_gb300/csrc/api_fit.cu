@@ -69,8 +69,6 @@ fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n)
   if (!(p.ratio_floor > 0.f)) return fail(ctx, FKK_ERR_INVALID_ARG, "ratio_floor must be > 0");
   if (p.precision != FKK_PREC_BF16X3) return fail(ctx, FKK_ERR_INVALID_ARG, "unknown precision");
   if (p.noise_alpha < 0.0 || p.noise_sigma_g < 0.0) return fail(ctx, FKK_ERR_INVALID_ARG, "negative noise parameter");
-  if (!(p.eig_tol >= 0.0 && p.eig_tol < 1.0)) return fail(ctx, FKK_ERR_INVALID_ARG, "eig_tol must be in [0, 1)");
-  if (p.eig_max_sweeps < 0 || p.eig_max_sweeps > 1000) return fail(ctx, FKK_ERR_INVALID_ARG, "bad eig_max_sweeps");
   return FKK_OK;
 }
 
@@ -161,8 +159,6 @@ void fkk_fit_params_default(fkk_fit_params* p) {
   p->ratio_floor = 1e-6f;
   p->noise_alpha = 0.0;
   p->noise_sigma_g = 0.0;
-  p->eig_tol = 0.0;
-  p->eig_max_sweeps = 0;
 }
 
 fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
@@ -209,7 +205,7 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   stage_mark(ctx, 1, st);
   if ((s = launch_gram(ctx, D, B->f, G, st))) return bail(s);
   stage_mark(ctx, 2, st);
-  if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st, nullptr, p.eig_tol, p.eig_max_sweeps))) return bail(s);
+  if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
   FKK_COUNT_LAUNCH(); s_and_w_kernel<<<k, 256, 0, st>>>(B->lam, B->v, m, k, p.ml_lambda, B->s, B->w);
   float* P = (float*)workspace(ctx, "fit_p", (size_t)n * k * 4, &s);
   if (!P) return bail(s);
@@ -222,7 +218,7 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   if (!nq_dev) return bail(s);
   double* xr = (double*)workspace(ctx, "fit_xrows", (size_t)2 * k * k * 8, &s);
   if (!xr) return bail(s);
-  if ((s = launch_gather_q(ctx, qm, qm + k, k, P, B->q, nq_dev, xr, st))) return bail(s);
+  if ((s = launch_gather_q(ctx, qm, qm + k, k, P, n, B->q, nq_dev, xr, st))) return bail(s);
   if ((s = cuda_check(ctx, cudaMemcpyAsync(B->nq, nq_dev, sizeof(int), cudaMemcpyDeviceToDevice, st), "nq"))) return bail(s);
   BasisOut bo{B->c_amp, B->c_ph, B->b, B->h_b, B->phi_pec_t, B->h_phi, B->v_sec_t};
   if ((s = launch_basis_math(ctx, basis_params(p, m, L), B->v, B->f, xr, 2 * k, bo, st))) return bail(s);
@@ -380,14 +376,14 @@ fkk_status fkk_gram(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int
   return launch_gram(ctx, D, f, g_out, st);
 }
 
-fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double tol, int32_t max_sweeps,
-                        double* lam, double* v, void* stream) {
+fkk_status fkk_eig_topk(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, double* lam, double* v,
+                        void* stream) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  if (!g || !lam || !v || m < 2 || m > 2048 || k < 1 || k > 80 || k > m || !(tol >= 0.0 && tol < 1.0) || max_sweeps < 0 || max_sweeps > 1000)
+  if (!g || !lam || !v || m < 2 || m > 2048 || k < 1 || k > 80 || k > m)
     return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_eig_topk: bad arguments");
   FKK_TRY(bind(ctx));
-  return launch_eig_topk(ctx, g, m, k, lam, v, as_stream(stream), nullptr, tol, max_sweeps);
+  return launch_eig_topk(ctx, g, m, k, lam, v, as_stream(stream));
 }
 
 fkk_status fkk_project(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,

@@ -15,11 +15,18 @@ namespace {
 
 // ------------------------------------------------------------------ q ---
 __global__ void gather_q_kernel(const int64_t* __restrict__ qmax, const int64_t* __restrict__ qmin, int k,
-                                int64_t* __restrict__ q, int* __restrict__ nq) {
+                                int64_t n_rows, int64_t* __restrict__ q, int* __restrict__ nq, long long* status) {
   if (threadIdx.x != 0) return;
   int64_t buf[160];
   int n = 0;
   for (int i = 0; i < k; ++i) { buf[n++] = qmax[i]; buf[n++] = qmin[i]; }
+  // a column of P without a finite value has no extreme row: report it and
+  // use row 0 rather than index past P
+  for (int a = 0; a < n; ++a)
+    if (buf[a] < 0 || buf[a] >= n_rows) {
+      record_error(status, kErrNotConverged);
+      buf[a] = 0;
+    }
   for (int a = 1; a < n; ++a) {  // insertion sort
     int64_t v = buf[a];
     int b = a - 1;
@@ -445,8 +452,8 @@ __global__ void axpy3_kernel(const double* __restrict__ a, const double* __restr
 }  // namespace
 
 fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
-                           int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st) {
-  FKK_COUNT_LAUNCH(); gather_q_kernel<<<1, 32, 0, st>>>(qmax, qmin, k, q, nq_dev);
+                           int64_t n_rows, int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st) {
+  FKK_COUNT_LAUNCH(); gather_q_kernel<<<1, 32, 0, st>>>(qmax, qmin, k, n_rows, q, nq_dev, ctx->d_status);
   FKK_COUNT_LAUNCH(); gather_rows_kernel<<<2 * k, 32, 0, st>>>(p, k, q, nq_dev, x_rows);
   return cuda_check(ctx, cudaGetLastError(), "gather_q launch");
 }

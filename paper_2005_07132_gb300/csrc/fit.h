@@ -49,10 +49,8 @@ fkk_status launch_noise_scale(fkk_ctx* ctx, const double* sum_i, int64_t n, int 
 
 // Top-k eigenpairs of the symmetric m x m fp64 G: lam (k, descending) and
 // V (m x k, row-major), each column's largest-magnitude entry positive.
-// *sweeps_out (host pointer, optional) receives the Jacobi sweep count once
-// the stream reaches it.
 fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* lam, double* v,
-                           cudaStream_t st, int* sweeps_out, double tol32 = 0.0, int max_sweeps32 = 0);
+                           cudaStream_t st);
 
 // P = A W (n x k fp32, ld k) from the transformed cube, with A = (d + c) f
 // folded into W: P[n,i] = sum_j d[n,j] Wf[j,i] + o_i, Wf = f W, o = c^T Wf.
@@ -94,7 +92,7 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
 // q = sorted unique(qmax U qmin) (device int64, up to 2k), count to *nq_dev;
 // x_rows[r, :] = (double) P[q[r], :].
 fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
-                           int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st);
+                           int64_t n_rows, int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st);
 
 // Out = exp(P C_amp) sin(P C_ph) (and cos for re_out), P n x k fp32.
 fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,

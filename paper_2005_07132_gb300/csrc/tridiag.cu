@@ -1,0 +1,990 @@
+// Symmetric eigensolve of the Gram matrix for its k largest eigenpairs
+// (Sec. 2.2: V and S of the SVD of A follow from G = A^T A = V S^2 V^T):
+//   1. Householder reduction Q^T G Q = T to symmetric tridiagonal form in one
+//      persistent cooperative kernel with a single grid barrier per column;
+//   2. the k largest eigenvalues of T by Sturm-count multisection;
+//   3. one eigenvector of T per eigenvalue from the twisted factorisation of
+//      T - lambda I (the index where the eigenvector is largest is found
+//      from the two one-sided factorisations, and the vector follows from
+//      products of their ratios);
+//   4. V = Q Z with the reflectors applied 32 at a time in the compact WY
+//      form I - Y T Y^T, then a Cholesky-QR pass in fp64 and the sign
+//      convention (largest-magnitude component positive).
+// Steps 1-4 run in double-word arithmetic on the fp32 pipe (df64.cuh, about
+// 48 significant bits) on G scaled by a power of two; fp64 is used only to
+// read G and for the final Cholesky QR.
+//
+// Reduction, step j (reflector H_j = I - tau v v^T, v[j+1] = 1, zero above):
+//   p = tau A v,  w = p - (tau/2)(p.v) v,  A <- A - v w^T - w v^T
+// on the trailing rows/columns j+1..m-1.  Column c belongs to CTA c mod G and
+// stays in its shared memory (global memory when the matrix is too large);
+// warp s of a CTA updates its s-th column.  Every CTA forms the next
+// reflector itself: the owner of column j+1 has published that column before
+// the barrier, and with the full p every CTA can apply step j's update to it.
+// The dot products p of the next step are accumulated while the columns are
+// updated, so a step is one pass over the owned columns and one barrier.
+#include <algorithm>
+
+#include "common.cuh"
+#include "df64.cuh"
+#include "fit.h"
+
+namespace fkk {
+namespace {
+
+using dw::df;
+
+constexpr int kTrThreads = 512;
+constexpr int kTrWarps = kTrThreads / 32;
+constexpr int kVecWarps = 8;  // warps that run the length-m vector phases
+constexpr int kVecThreads = kVecWarps * 32;
+constexpr int kMaxLoc = kTrWarps;  // columns per CTA (one warp each): m <= kMaxLoc * grid
+constexpr int kWY = 32;            // reflectors per block in the back-transformation
+constexpr int kBtThreads = 512;
+constexpr int kBisWarps = 8;       // multisection points per round: 32 * kBisWarps
+constexpr float kEpsF = 5.9604645e-08f;  // 2^-24
+
+// Sum over the vector warps; thread 0 gets the total.
+__device__ __forceinline__ df vec_sum_to0(df x, df* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < kVecWarps) {
+    x = dw::warp_sum(x);
+    if (lane == 0) red[warp] = x;
+  }
+  __syncthreads();
+  df t = dw::make(0.f);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kVecWarps; ++q) t = dw::add(t, red[q]);
+  return t;
+}
+
+// Reflector from alpha (first entry) and sigma = sum of squares of the rest
+// (LAPACK dlarfg convention): H x = beta e_1, tau = (beta - alpha) / beta,
+// v = x / (alpha - beta) below the first entry.  sc = {tau, beta, scal}.
+__device__ __forceinline__ void reflector(df alp, df sig, df* sc) {
+  if (sig.h == 0.f) {
+    sc[0] = dw::make(0.f);
+    sc[1] = alp;
+    sc[2] = dw::make(0.f);
+    return;
+  }
+  const df mu = dw::sqrt(dw::add(dw::mul(alp, alp), sig));
+  const df beta = alp.h <= 0.f ? mu : dw::neg(mu);
+  sc[0] = dw::div(dw::sub(beta, alp), beta);
+  sc[1] = beta;
+  sc[2] = dw::rcp(dw::sub(alp, beta));
+}
+
+struct TridArgs {
+  const double* g;  // m x m symmetric, row-major (row c = column c)
+  int m;
+  int ncol_max;     // ceil(m / grid)
+  df* work;         // m x m working columns when they do not fit in shared memory
+  df* pbuf;         // [2][m] p of the next step, by column
+  df* cbuf;         // [2][m] next pivot column before the current step's update
+  df* d;            // [m] diagonal of T (scaled)
+  df* e;            // [m] sub-diagonal of T (scaled; e[m-1] = 0)
+  df* tau;          // [m] reflector scalars
+  df* u;            // [m][m] row j = reflector vector of step j
+  unsigned* maxbits;  // max |G| as float bits (atomicMax), zeroed by the host
+  int* ex_out;      // T = 2^ex Ts
+  long long* cycles;  // optional [8]: SM clock cycles of CTA 0 per phase
+  unsigned* bar;
+  int* abort_flag;
+  long long* status;
+};
+
+template <bool kSmem>
+__global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
+  extern __shared__ df smd[];
+  const int m = a.m, nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const bool vecw = warp < kVecWarps;
+  const int nloc = (m - b + nb - 1) / nb;  // own columns c = b + s * nb
+  df* cols = smd;
+  df* v = smd + (kSmem ? (size_t)a.ncol_max * m : 0);
+  df* vn = v + m;
+  df* w = vn + m;
+  df* red = w + m;   // [32]
+  df* sc = red + 32; // [8] scalars
+  __shared__ float fmax_s[kTrWarps];
+  __shared__ int ex_s;
+  unsigned target = 0;
+  auto colp = [&](int s) -> df* {
+    return kSmem ? cols + (size_t)s * m : a.work + (size_t)(b + s * nb) * m;
+  };
+  const bool timed = a.cycles != nullptr && b == 0 && tid == 0;
+  long long cyc[5] = {0, 0, 0, 0, 0};
+  long long t_prev = timed ? clock64() : 0;
+  auto mark = [&](int ph) {
+    if (timed) {
+      const long long t = clock64();
+      cyc[ph] += t - t_prev;
+      t_prev = t;
+    }
+  };
+
+  // own columns in double-word, and max |G| over the whole matrix
+  float mx = 0.f;
+  for (int s = 0; s < nloc; ++s) {
+    const double* src = a.g + (size_t)(b + s * nb) * m;
+    df* dst = colp(s);
+    for (int i = tid; i < m; i += kTrThreads) {
+      const df x = dw::from_double(src[i]);
+      dst[i] = x;
+      mx = fmaxf(mx, fabsf(x.h));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) fmax_s[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int q = 0; q < kTrWarps; ++q) t = fmaxf(t, fmax_s[q]);
+    atomicMax(a.maxbits, __float_as_uint(t));
+  }
+  if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
+  mark(4);
+  if (tid == 0) {
+    const float t = __uint_as_float(__ldcg(a.maxbits));
+    ex_s = t > 0.f ? ilogbf(t) : 0;
+    if (b == 0) *a.ex_out = ex_s;
+  }
+  __syncthreads();
+  const int ex = ex_s;
+  for (int s = 0; s < nloc; ++s) {
+    df* col = colp(s);
+    for (int i = tid; i < m; i += kTrThreads) col[i] = dw::ldexp(col[i], -ex);
+  }
+  if (m <= 2) {
+    if (b == 0 && tid == 0) {
+      a.d[0] = dw::ldexp(dw::from_double(a.g[0]), -ex);
+      a.e[0] = dw::make(0.f);
+      if (m == 2) {
+        a.d[1] = dw::ldexp(dw::from_double(a.g[3]), -ex);
+        a.e[0] = dw::ldexp(dw::from_double(a.g[2]), -ex);
+      }
+    }
+    return;
+  }
+
+  // reflector of step 0 from column 0
+  {
+    df sig = dw::make(0.f), alp = dw::make(0.f);
+    if (vecw)
+      for (int i = tid; i < m; i += kVecThreads) {
+        const df x = i >= 1 ? dw::ldexp(dw::from_double(a.g[i]), -ex) : dw::make(0.f);
+        vn[i] = x;
+        if (i >= 2) sig = dw::add(sig, dw::mul(x, x));
+      }
+    sig = vec_sum_to0(sig, red);
+    if (tid == 0) {
+      alp = vn[1];
+      reflector(alp, sig, sc);
+      if (b == 0) {
+        a.d[0] = dw::ldexp(dw::from_double(a.g[0]), -ex);
+        a.e[0] = sc[1];
+        a.tau[0] = sc[0];
+      }
+    }
+    __syncthreads();
+    const df scal = sc[2];
+    if (vecw)
+      for (int i = tid; i < m; i += kVecThreads) {
+        const df x = i < 1 ? dw::make(0.f) : (i == 1 ? dw::make(1.f) : dw::mul(vn[i], scal));
+        v[i] = x;
+        if (b == 0) a.u[i] = x;
+      }
+    __syncthreads();
+    // p of step 0 and the copy of column 1: warp s takes own column s
+    const df tau0 = sc[0];
+    if (warp < nloc) {
+      const int c = b + warp * nb;
+      const df* col = colp(warp);
+      df acc = dw::make(0.f);
+      if (c >= 1)
+        for (int i = 1 + lane; i < m; i += 32) {
+          const df x = col[i];
+          acc = dw::add(acc, dw::mul(x, v[i]));
+          if (c == 1) a.cbuf[i] = x;
+        }
+      acc = dw::warp_sum(acc);
+      if (lane == 0 && c >= 1) a.pbuf[c] = dw::mul(tau0, acc);
+    }
+  }
+  df tau_cur = sc[0];
+  mark(0);
+  if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
+  mark(4);
+
+  const int nsteps = m - 2;
+  for (int j = 0; j < nsteps; ++j) {
+    const int buf = j & 1, nxt = buf ^ 1;
+    const df* pb = a.pbuf + (size_t)buf * m;
+    const df* cb = a.cbuf + (size_t)buf * m;
+    // 1. w = p - (tau/2)(p.v) v on rows >= j+1
+    df dot = dw::make(0.f);
+    if (vecw)
+      for (int i = tid; i < m; i += kVecThreads) {
+        df p = dw::make(0.f);
+        if (i >= j + 1) {
+          const float2 t = __ldcg(reinterpret_cast<const float2*>(pb + i));
+          p = dw::make(t.x, t.y);
+          dot = dw::add(dot, dw::mul(p, v[i]));
+        }
+        w[i] = p;
+      }
+    dot = vec_sum_to0(dot, red);
+    if (tid == 0) sc[4] = dw::mul(dw::mul(tau_cur, dot), 0.5f);
+    __syncthreads();
+    const df halfk = sc[4];
+    if (vecw)
+      for (int i = tid; i < m; i += kVecThreads)
+        if (i >= j + 1) w[i] = dw::fnma(halfk, v[i], w[i]);
+    __syncthreads();
+    mark(1);
+    // 2. pivot column j+1 after this step; the next reflector from it
+    const df wj1 = w[j + 1];
+    const bool last = (j + 1 > m - 3);
+    df sig = dw::make(0.f);
+    if (vecw)
+      for (int i = tid; i < m; i += kVecThreads) {
+        if (i < j + 1) continue;
+        const float2 t = __ldcg(reinterpret_cast<const float2*>(cb + i));
+        const df x = dw::sub(dw::fnma(v[i], wj1, dw::make(t.x, t.y)), w[i]);
+        vn[i] = x;
+        if (i == j + 1 && b == 0) a.d[j + 1] = x;
+        if (last) {
+          if (i == m - 1 && b == 0) a.e[m - 2] = x;
+        } else if (i >= j + 3) {
+          sig = dw::add(sig, dw::mul(x, x));
+        }
+      }
+    df tau_nxt = dw::make(0.f);
+    if (!last) {
+      sig = vec_sum_to0(sig, red);
+      if (tid == 0) {
+        reflector(vn[j + 2], sig, sc);
+        if (b == 0) {
+          a.e[j + 1] = sc[1];
+          a.tau[j + 1] = sc[0];
+        }
+      }
+      __syncthreads();
+      tau_nxt = sc[0];
+      const df scal = sc[2];
+      if (vecw)
+        for (int i = tid; i < m; i += kVecThreads) {
+          df x;
+          if (i < j + 2) x = dw::make(0.f);
+          else if (i == j + 2) x = dw::make(1.f);
+          else x = dw::mul(vn[i], scal);
+          vn[i] = x;
+          if (b == 0) a.u[(size_t)(j + 1) * m + i] = x;
+        }
+    }
+    __syncthreads();
+    mark(2);
+    // 3. warp s updates own column s (c >= j+2) on rows >= j+2 and
+    //    accumulates p of the next step
+    if (warp < nloc) {
+      const int c = b + warp * nb;
+      if (c >= j + 2) {
+        df* col = colp(warp);
+        const df wc = w[c], vc = v[c];
+        df acc = dw::make(0.f);
+        df* cnext = a.cbuf + (size_t)nxt * m;
+        for (int i = j + 2 + lane; i < m; i += 32) {
+          const df x = dw::sub(col[i], dw::add(dw::mul(v[i], wc), dw::mul(w[i], vc)));
+          col[i] = x;
+          if (!last) acc = dw::add(acc, dw::mul(x, vn[i]));
+          if (c == j + 2) cnext[i] = x;
+          if (last && i == m - 1) a.d[m - 1] = x;  // c == m - 1 here
+        }
+        if (!last) {
+          acc = dw::warp_sum(acc);
+          if (lane == 0) a.pbuf[(size_t)nxt * m + c] = dw::mul(tau_nxt, acc);
+        }
+      }
+    }
+    mark(3);
+    if (last) break;
+    df* tmp = v;
+    v = vn;
+    vn = tmp;
+    tau_cur = tau_nxt;
+    if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
+    mark(4);
+  }
+  if (timed)
+    for (int q = 0; q < 5; ++q) a.cycles[q] = cyc[q];
+}
+
+// ---------------------------------------------------------------------------
+// Tridiagonal eigenvalues and eigenvectors on Ts (largest entry below 2).
+// Off-diagonals below 2^-46 sqrt(|d_i d_{i+1}|) are set to zero (the matrix
+// splits there).
+
+struct TriBounds {
+  float gl, gu;  // Gershgorin bounds, widened
+};
+
+// Loads ds, es (es[m-1] = 0) and eb[i] = es[i-1]^2 (eb[0] = 0) into shared
+// memory; any number of warps.
+__device__ TriBounds load_tri(const df* __restrict__ d, const df* __restrict__ e, int m, df* ds, df* es, df* eb,
+                              float* redf) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ds[i] = d[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    df x = dw::make(0.f);
+    if (i < m - 1) {
+      x = e[i];
+      if (fabsf(x.h) <= 1.4210855e-14f * sqrtf(fabsf(ds[i].h) * fabsf(ds[i + 1].h))) x = dw::make(0.f);
+    }
+    es[i] = x;
+  }
+  __syncthreads();
+  float lo = 3e38f, hi = -3e38f;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const df el = i > 0 ? es[i - 1] : dw::make(0.f);
+    eb[i] = dw::mul(el, el);
+    const float r = fabsf(el.h) + fabsf(es[i].h);
+    lo = fminf(lo, ds[i].h - r);
+    hi = fmaxf(hi, ds[i].h + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    redf[warp] = lo;
+    redf[32 + warp] = hi;
+  }
+  __syncthreads();
+  TriBounds t;
+  t.gl = 3e38f;
+  t.gu = -3e38f;
+  for (int q = 0; q < nw; ++q) {
+    t.gl = fminf(t.gl, redf[q]);
+    t.gu = fmaxf(t.gu, redf[32 + q]);
+  }
+  const float wid = (fabsf(t.gl) + fabsf(t.gu)) * 1e-5f + 1e-30f;
+  t.gl -= wid;
+  t.gu += wid;
+  __syncthreads();
+  return t;
+}
+
+// Number of eigenvalues of Ts below x: sign changes of the leading principal
+// minors of Ts - x I (three-term recurrence; an exact zero minor counts as a
+// tiny negative pivot).  The minors can shrink by the ratio of the smallest
+// to the largest diagonal entry at every step, so the pair is rescaled by a
+// power of two whenever the larger leaves [2^-32, 2^32]: the float exponent
+// of a double-word would otherwise underflow within a few steps.
+__device__ __forceinline__ int sturm_count(const df* ds, const df* eb, int m, df x) {
+  df p2 = dw::make(1.f);
+  df p1 = dw::sub(ds[0], x);
+  if (p1.h == 0.f) p1 = dw::make(-0x1p-60f);
+  int cnt = dw::lt0(p1);
+  for (int i = 1; i < m; ++i) {
+    df p = dw::sub(dw::mul(dw::sub(ds[i], x), p1), dw::mul(eb[i], p2));
+    if (p.h == 0.f) p = dw::mul(p1, -0x1p-60f);
+    cnt += dw::lt0(p) != dw::lt0(p1);
+    p2 = p1;
+    p1 = p;
+    const float mxp = fmaxf(fabsf(p1.h), fabsf(p2.h));
+    if (mxp > 0x1p32f || mxp < 0x1p-32f) {
+      const int sh = ilogbf(mxp);
+      p1 = dw::ldexp(p1, -sh);
+      p2 = dw::ldexp(p2, -sh);
+    }
+  }
+  return cnt;
+}
+
+// One CTA per eigenvalue: rank r = m-1-c (c = 0 the largest).  Each round
+// evaluates 32 * kBisWarps interior points of the bracket [lo, hi]
+// (N(lo) <= r < N(hi)) and keeps the sub-interval where the count crosses r.
+__global__ void __launch_bounds__(kBisWarps * 32) tri_bisect_kernel(const df* __restrict__ d,
+                                                                    const df* __restrict__ e, int m,
+                                                                    df* __restrict__ lam) {
+  extern __shared__ df smd[];
+  df* ds = smd;
+  df* es = ds + m;
+  df* eb = es + m;
+  __shared__ float redf[64];
+  __shared__ int first_s[kBisWarps];
+  __shared__ df lohi[2];
+  const int P = kBisWarps * 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x;
+  const int r = m - 1 - c;
+  const TriBounds t = load_tri(d, e, m, ds, es, eb, redf);
+  df lo = dw::make(t.gl), hi = dw::make(t.gu);
+  const float tol = 8.f * kEpsF * kEpsF * fmaxf(fabsf(t.gl), fabsf(t.gu));
+  for (int round = 0; round < 24; ++round) {
+    const df wid = dw::sub(hi, lo);
+    if (wid.h <= tol) break;
+    const float f = (float)(tid + 1) / (float)(P + 1);
+    const df x = dw::add(lo, dw::mul(wid, f));
+    const int n = sturm_count(ds, eb, m, x);
+    const unsigned above = __ballot_sync(0xffffffffu, n > r);
+    if (lane == 0) first_s[warp] = above ? __ffs(above) - 1 : 32;
+    __syncthreads();
+    // first point (in block order) whose count exceeds r
+    int first = P;
+    for (int q = 0; q < kBisWarps; ++q)
+      if (first_s[q] < 32) {
+        first = q * 32 + first_s[q];
+        break;
+      }
+    if (tid == first - 1) lohi[0] = x;
+    if (tid == first) lohi[1] = x;
+    __syncthreads();
+    if (first > 0) lo = lohi[0];
+    if (first < P) hi = lohi[1];
+    __syncthreads();
+  }
+  if (tid == 0) lam[c] = dw::mul(dw::add(lo, hi), 0.5f);
+}
+
+// One warp per eigenvalue: eigenvector of Ts from the twisted factorisation
+// of Ts - lambda I.  D+ (top-down) and D- (bottom-up) pivots; the twist index
+// r minimises |gamma_r| = |D+_r + D-_r - (ds_r - lambda)|; then z_r = 1,
+// z_i = -(es_i / D+_i) z_{i+1} above r and z_i = -(es_{i-1} / D-_i) z_{i-1}
+// below.  Equal eigenvalues of a split matrix take the blocks in order of
+// their smallest |gamma|.
+__global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, const df* __restrict__ e, int m,
+                                                     int k, const df* __restrict__ lam, df* __restrict__ z_out,
+                                                     long long* status) {
+  extern __shared__ df smd[];
+  df* ds = smd;
+  df* es = ds + m;
+  df* eb = es + m;
+  df* dp = eb + m;
+  df* dm = dp + m;
+  double* z = reinterpret_cast<double*>(dm + m);
+  __shared__ float redf[64];
+  const int lane = threadIdx.x;
+  const int c = blockIdx.x;
+  const TriBounds t = load_tri(d, e, m, ds, es, eb, redf);
+  // eigenvalues equal to within the bisection tolerance form a group; every
+  // member computes with the group's first value, so all rank the blocks of
+  // a split matrix alike and member t takes the t-th
+  const float dup_tol = 16.f * kEpsF * kEpsF * fmaxf(fabsf(t.gl), fabsf(t.gu));
+  int q0 = c;
+  while (q0 > 0 && fabsf(dw::sub(lam[q0 - 1], lam[c]).h) <= dup_tol) --q0;
+  const df ls = lam[q0];
+  const int dup = c - q0;
+  const float tiny = 0x1p-90f;
+  if (lane == 0) {
+    df x = dw::sub(ds[0], ls);
+    if (fabsf(x.h) < tiny) x = dw::make(-tiny);
+    dp[0] = x;
+    for (int i = 1; i < m; ++i) {
+      x = dw::sub(dw::sub(ds[i], ls), dw::div(eb[i], x));
+      if (fabsf(x.h) < tiny) x = dw::make(-tiny);
+      dp[i] = x;
+    }
+  } else if (lane == 1) {
+    df x = dw::sub(ds[m - 1], ls);
+    if (fabsf(x.h) < tiny) x = dw::make(-tiny);
+    dm[m - 1] = x;
+    for (int i = m - 2; i >= 0; --i) {
+      x = dw::sub(dw::sub(ds[i], ls), dw::div(eb[i + 1], x));
+      if (fabsf(x.h) < tiny) x = dw::make(-tiny);
+      dm[i] = x;
+    }
+  }
+  __syncwarp();
+  auto gamma_abs = [&](int i) -> float {
+    return fabsf(dw::sub(dw::add(dp[i], dm[i]), dw::sub(ds[i], ls)).h);
+  };
+  float best = 3e38f;
+  int bi = 0x7fffffff;
+  for (int i = lane; i < m; i += 32) {
+    const float gam = gamma_abs(i);
+    if (gam < best) { best = gam; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov < best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  int r = bi;
+  if (dup > 0) {
+    // blocks of the split matrix ranked by their smallest |gamma|; take the
+    // (dup)-th
+    int chosen = r;
+    if (lane == 0) {
+      float prev_v = -1.f;
+      int prev_i = -1;
+      for (int pick = 0; pick <= dup; ++pick) {
+        float bv = 3e38f;
+        int bidx = -1;
+        int s0 = 0;
+        while (s0 < m) {
+          int s1 = s0;
+          while (s1 < m - 1 && es[s1].h != 0.f) ++s1;
+          float mv = 3e38f;
+          int mi = s0;
+          for (int i = s0; i <= s1; ++i) {
+            const float gam = gamma_abs(i);
+            if (gam < mv) { mv = gam; mi = i; }
+          }
+          const bool after_prev = mv > prev_v || (mv == prev_v && mi > prev_i);
+          if (after_prev && (mv < bv || (mv == bv && mi < bidx))) { bv = mv; bidx = mi; }
+          s0 = s1 + 1;
+        }
+        if (bidx < 0) break;
+        chosen = bidx;
+        prev_v = bv;
+        prev_i = bidx;
+      }
+    }
+    r = __shfl_sync(0xffffffffu, chosen, 0);
+  }
+  if (r < 0 || r >= m) {  // no finite |gamma|: report, fall back to index 0
+    if (lane == 0) record_error(status, kErrNotConverged);
+    r = 0;
+  }
+  // ratios (in place), then the two product chains in fp64: a pivot at the
+  // floor gives a ratio near 2^90, beyond what the float exponent of a
+  // double-word can carry through a product chain
+  for (int i = lane; i < m; i += 32) {
+    if (i < r) dp[i] = dw::neg(dw::div(es[i], dp[i]));
+    else if (i > r) dm[i] = dw::neg(dw::div(es[i - 1], dm[i]));
+  }
+  __syncwarp();
+  if (lane == 0) {
+    z[r] = 1.0;
+    double x = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+      x = fabs(x) < 1e-280 ? 0.0 : dw::to_double(dp[i]) * x;
+      z[i] = x;
+    }
+  } else if (lane == 1) {
+    double x = 1.0;
+    for (int i = r + 1; i < m; ++i) {
+      x = fabs(x) < 1e-280 ? 0.0 : dw::to_double(dm[i]) * x;
+      z[i] = x;
+    }
+  }
+  __syncwarp();
+  double nrm = 0.0;
+  for (int i = lane; i < m; i += 32) nrm = fma(z[i], z[i], nrm);
+  nrm = warp_sum(nrm);
+  if (!(nrm >= 1.0 && nrm < 1e300)) {  // z[r] = 1, so nrm >= 1 unless something overflowed
+    if (lane == 0) record_error(status, kErrNotConverged);
+    for (int i = lane; i < m; i += 32) z_out[(size_t)i * k + c] = dw::make(i == r ? 1.f : 0.f);
+    return;
+  }
+  const double inv = 1.0 / sqrt(nrm);
+  for (int i = lane; i < m; i += 32) z_out[(size_t)i * k + c] = dw::from_double(z[i] * inv);
+}
+
+// ---------------------------------------------------------------------------
+// Back-transformation V = Q Z, Q = H_0 H_1 ... H_{m-3}, blocks of 32
+// reflectors B_b = I - Y_b T_b Y_b^T (T_b upper triangular), applied from the
+// last block to the first.  Cooperative: rows are split evenly over the CTAs.
+// The result is written in fp64.
+
+struct BackArgs {
+  const df* u;    // [m][m] reflector rows
+  const df* tau;  // [nrefl]
+  int m, nrefl, k, nbk, S;
+  df* z;          // [m][k] in / out
+  double* v;      // [m][k] result
+  df* gpart;      // [nbk][S][32 * 32]
+  df* tblk;       // [nbk][32 * 32]
+  df* wpart;      // [grid][32 * k]
+  df* wfull;      // [32 * k]
+  unsigned* bar;
+  int* abort_flag;
+  long long* status;
+};
+
+__global__ void __launch_bounds__(kBtThreads, 1) back_wy_kernel(BackArgs a) {
+  extern __shared__ df smd[];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int m = a.m, k = a.k;
+  unsigned target = 0;
+  // phase 0: partial Gram matrices Y_b^T Y_b over row slices
+  if (cta < a.nbk * a.S) {
+    df* ys = smd;  // [32 rows][kWY]
+    const int b = cta / a.S, part = cta % a.S;
+    const int j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
+    const int rbeg = j0 + 1, rows = m - rbeg;
+    const int per = (rows + a.S - 1) / a.S;
+    const int i0 = rbeg + part * per, i1 = min(m, i0 + per);
+    df acc0 = dw::make(0.f), acc1 = dw::make(0.f);
+    const int np = kWY * (kWY + 1) / 2;
+    int p0 = -1, q0 = -1, p1 = -1, q1 = -1;
+    for (int idx = tid, t = 0; idx < np && t < 2; idx += kBtThreads, ++t) {
+      int p = 0, rem = idx;
+      while (rem >= kWY - p) { rem -= kWY - p; ++p; }
+      if (t == 0) { p0 = p; q0 = p + rem; } else { p1 = p; q1 = p + rem; }
+    }
+    for (int base = i0; base < i1; base += 32) {
+      __syncthreads();
+      for (int x = tid; x < 32 * kWY; x += kBtThreads) {
+        const int rr = x / kWY, p = x % kWY, i = base + rr;
+        ys[rr * kWY + p] = (i < i1 && p < nr) ? a.u[(size_t)(j0 + p) * m + i] : dw::make(0.f);
+      }
+      __syncthreads();
+      const int nrr = min(32, i1 - base);
+      for (int rr = 0; rr < nrr; ++rr) {
+        if (p0 >= 0) acc0 = dw::add(acc0, dw::mul(ys[rr * kWY + p0], ys[rr * kWY + q0]));
+        if (p1 >= 0) acc1 = dw::add(acc1, dw::mul(ys[rr * kWY + p1], ys[rr * kWY + q1]));
+      }
+    }
+    df* gp = a.gpart + ((size_t)b * a.S + part) * kWY * kWY;
+    if (p0 >= 0) gp[p0 * kWY + q0] = acc0;
+    if (p1 >= 0) gp[p1 * kWY + q1] = acc1;
+  }
+  if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
+  // phase 1: T_b by the forward recurrence T[0:i, i] = -tau_i T[0:i, 0:i] (Y^T y_i)
+  if (cta < a.nbk) {
+    df* gs = smd;                 // [32][32]
+    df* ts = gs + kWY * kWY;      // [32][32]
+    df* tmp = ts + kWY * kWY;     // [32]
+    const int b = cta, j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
+    for (int x = tid; x < kWY * kWY; x += kBtThreads) {
+      const int p = x / kWY, q = x % kWY;
+      df s = dw::make(0.f);
+      if (p <= q)
+        for (int part = 0; part < a.S; ++part) s = dw::add(s, a.gpart[((size_t)b * a.S + part) * kWY * kWY + x]);
+      gs[x] = s;
+      ts[x] = dw::make(0.f);
+    }
+    __syncthreads();
+    for (int i = 0; i < nr; ++i) {
+      const df ti = a.tau[j0 + i];
+      if (tid < i) tmp[tid] = dw::neg(dw::mul(ti, gs[tid * kWY + i]));
+      __syncthreads();
+      df s = dw::make(0.f);
+      if (tid < i)
+        for (int q = tid; q < i; ++q) s = dw::add(s, dw::mul(ts[tid * kWY + q], tmp[q]));
+      __syncthreads();
+      if (tid < i) ts[tid * kWY + i] = s;
+      if (tid == 0) ts[i * kWY + i] = ti;
+      __syncthreads();
+    }
+    for (int x = tid; x < kWY * kWY; x += kBtThreads) a.tblk[(size_t)b * kWY * kWY + x] = ts[x];
+  }
+  if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
+  // phase 2: blocks from last to first on a fixed row partition
+  const int per = (m + G - 1) / G;
+  const int r0 = cta * per, r1 = min(m, r0 + per);
+  df* ys = smd;                        // [per][kWY]
+  df* zs = ys + (size_t)per * kWY;     // [per][k]
+  df* wsm = zs + (size_t)per * k;      // [kWY][k]
+  df* wc = wsm + (size_t)kWY * k;      // [kWY]
+  df* wsl = wc + kWY;                  // [kBtThreads]
+  for (int x = tid; x < max(0, r1 - r0) * k; x += kBtThreads) zs[x] = a.z[(size_t)r0 * k + x];
+  for (int b = a.nbk - 1; b >= 0; --b) {
+    const int j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
+    const int lo = max(r0, j0 + 1);
+    const int nrow = max(0, r1 - lo);
+    const int off = lo - r0;  // first local row
+    // (a) Y^T Z over my rows
+    for (int x = tid; x < nrow * kWY; x += kBtThreads) {
+      const int rr = x / kWY, p = x % kWY;
+      ys[x] = p < nr ? a.u[(size_t)(j0 + p) * m + lo + rr] : dw::make(0.f);
+    }
+    __syncthreads();
+    df* wp = a.wpart + (size_t)cta * kWY * k;
+    for (int x = tid; x < kWY * k; x += kBtThreads) {
+      const int p = x / k, c = x % k;
+      df s = dw::make(0.f);
+      for (int rr = 0; rr < nrow; ++rr) s = dw::add(s, dw::mul(ys[rr * kWY + p], zs[(off + rr) * k + c]));
+      wp[x] = s;
+    }
+    if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
+    // (b) column c of W = sum over CTAs, then T_b W
+    for (int c = cta; c < k; c += G) {
+      {
+        const int p = tid % kWY, sl = tid / kWY, nsl = kBtThreads / kWY;
+        df s = dw::make(0.f);
+        for (int g2 = sl; g2 < G; g2 += nsl) {
+          const float2 t = __ldcg(reinterpret_cast<const float2*>(a.wpart + (size_t)g2 * kWY * k + p * k + c));
+          s = dw::add(s, dw::make(t.x, t.y));
+        }
+        wsl[sl * kWY + p] = s;
+      }
+      __syncthreads();
+      if (tid < kWY) {
+        df s = dw::make(0.f);
+        for (int sl = 0; sl < kBtThreads / kWY; ++sl) s = dw::add(s, wsl[sl * kWY + tid]);
+        wc[tid] = s;
+      }
+      __syncthreads();
+      if (tid < kWY) {
+        const df* tb = a.tblk + (size_t)b * kWY * kWY;
+        df s = dw::make(0.f);
+        for (int q = tid; q < kWY; ++q) s = dw::add(s, dw::mul(tb[tid * kWY + q], wc[q]));
+        a.wfull[tid * k + c] = s;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
+    // (c) Z -= Y (T W) on my rows
+    for (int x = tid; x < kWY * k; x += kBtThreads) {
+      const float2 t = __ldcg(reinterpret_cast<const float2*>(a.wfull + x));
+      wsm[x] = dw::make(t.x, t.y);
+    }
+    __syncthreads();
+    for (int x = tid; x < nrow * k; x += kBtThreads) {
+      const int rr = x / k, c = x % k;
+      df s = zs[(off + rr) * k + c];
+      for (int p = 0; p < kWY; ++p) s = dw::sub(s, dw::mul(ys[rr * kWY + p], wsm[p * k + c]));
+      zs[(off + rr) * k + c] = s;
+    }
+    __syncthreads();
+  }
+  for (int x = tid; x < max(0, r1 - r0) * k; x += kBtThreads) a.v[(size_t)r0 * k + x] = dw::to_double(zs[x]);
+}
+
+// Z (double-word) to fp64, for m <= 2 (no reflectors).
+__global__ void df_to_double_kernel(const df* __restrict__ z, int n, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = dw::to_double(z[i]);
+}
+
+// lam = 2^ex * lam_s in fp64.
+__global__ void lam_out_kernel(const df* __restrict__ lam_s, const int* __restrict__ ex, int k,
+                               double* __restrict__ lam) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < k) lam[c] = ldexp(dw::to_double(lam_s[c]), *ex);
+}
+
+// Cholesky QR: W = Z^T Z, W = R^T R, Z <- Z R^-1.
+
+__global__ void ztz_kernel(const double* __restrict__ z, int m, int k, double* __restrict__ w) {
+  const int p = blockIdx.y, q = blockIdx.x;
+  if (q < p) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s = fma(z[(size_t)i * k + p], z[(size_t)i * k + q], s);
+  __shared__ double red[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int x = 0; x < (int)(blockDim.x >> 5); ++x) t += red[x];
+    w[p * k + q] = t;
+    w[q * k + p] = t;
+  }
+}
+
+// One block: R (upper) with W = R^T R, then Rinv.  A pivot that has lost all
+// but 1e-20 of its column norm (linearly dependent vectors) is reported as
+// FKK_ERR_NOT_CONVERGED.
+__global__ void chol_inv_kernel(const double* __restrict__ w, int k, double* __restrict__ rinv,
+                                long long* status) {
+  extern __shared__ double sm[];
+  double* r = sm;           // [k][k]
+  double* ri = r + k * k;   // [k][k]
+  for (int x = threadIdx.x; x < k * k; x += blockDim.x) {
+    r[x] = w[x];
+    ri[x] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    __shared__ double piv;
+    if (threadIdx.x == 0) {
+      const double dj = r[j * k + j];
+      if (dj > 1e-20 * w[j * k + j] && dj < 1e300) {
+        piv = sqrt(dj);
+      } else {
+        record_error(status, kErrNotConverged);
+        piv = 1.0;
+      }
+      r[j * k + j] = piv;
+    }
+    __syncthreads();
+    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) r[j * k + q] /= piv;
+    __syncthreads();
+    for (int x = threadIdx.x; x < (k - j - 1) * (k - j - 1); x += blockDim.x) {
+      const int q1 = j + 1 + x / (k - j - 1), q2 = j + 1 + x % (k - j - 1);
+      if (q2 >= q1) r[q1 * k + q2] -= r[j * k + q1] * r[j * k + q2];
+    }
+    __syncthreads();
+  }
+  // Rinv column by column (R upper triangular): R X = I
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int p = c; p >= 0; --p) {
+      double s = p == c ? 1.0 : 0.0;
+      for (int q = p + 1; q <= c; ++q) s -= r[p * k + q] * ri[q * k + c];
+      ri[p * k + c] = s / r[p * k + p];
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < k * k; x += blockDim.x) rinv[x] = ri[x];
+}
+
+// V = Z Rinv (row by row; one warp per row).
+__global__ void apply_rinv_kernel(const double* __restrict__ z, int m, int k, const double* __restrict__ rinv,
+                                  double* __restrict__ v) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const double* zr = z + (size_t)row * k;
+  for (int c = lane; c < k; c += 32) {
+    double s = 0.0;
+    for (int p = 0; p <= c; ++p) s = fma(zr[p], rinv[p * k + c], s);
+    v[(size_t)row * k + c] = s;
+  }
+}
+
+// Sign convention: the largest-magnitude component of each column positive
+// (ties to the lowest row).  One block per column.
+__global__ void sign_fix_kernel(double* __restrict__ v, int m, int k, long long* status) {
+  __shared__ double bvs[32];
+  __shared__ int bis[32];
+  const int c = blockIdx.x;
+  double bv = -1.0;
+  int bi = 0x7fffffff;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double x = fabs(v[(size_t)j * k + c]);
+    if (x > bv || (x == bv && j < bi)) { bv = x; bi = j; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { bvs[threadIdx.x >> 5] = bv; bis[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int x = 1; x < (int)(blockDim.x >> 5); ++x)
+      if (bvs[x] > bvs[0] || (bvs[x] == bvs[0] && bis[x] < bis[0])) { bvs[0] = bvs[x]; bis[0] = bis[x]; }
+  }
+  __syncthreads();
+  if (bis[0] < 0 || bis[0] >= m) {  // no finite entry in the column
+    if (threadIdx.x == 0) record_error(status, kErrNotConverged);
+    return;
+  }
+  const double sgn = v[(size_t)bis[0] * k + c] < 0.0 ? -1.0 : 1.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) v[(size_t)j * k + c] *= sgn;
+}
+
+}  // namespace
+
+fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* lam, double* v,
+                           cudaStream_t st) {
+  fkk_status s;
+  const int nsm = ctx->sm_count;
+  // 1. tridiagonal reduction
+  int nb = std::min(nsm, m);
+  if (nb < 1) nb = 1;
+  const int ncol_max = (m + nb - 1) / nb;
+  if (ncol_max > kMaxLoc) return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: m = %d too large", m);
+  const size_t vec_bytes = (size_t)(3 * m + 32 + 8) * sizeof(df);
+  const size_t smem_cols = (size_t)ncol_max * m * sizeof(df) + vec_bytes;
+  const bool in_smem = smem_cols <= 200 * 1024;
+  const size_t smem_tr = in_smem ? smem_cols : vec_bytes;
+  df* wsd = (df*)workspace(ctx, "tri_vecs", (size_t)(4 * m + 3 * m + 2 * k + 64) * sizeof(df), &s);
+  if (!wsd) return s;
+  df* pbuf = wsd;
+  df* cbuf = pbuf + 2 * m;
+  df* dd = cbuf + 2 * m;
+  df* ee = dd + m;
+  df* tau = ee + m;
+  df* lam_s = tau + m;
+  unsigned* scr = (unsigned*)workspace(ctx, "tri_bar", 256, &s);
+  if (!scr) return s;
+  df* u = (df*)workspace(ctx, "tri_u", (size_t)m * m * sizeof(df), &s);
+  if (!u) return s;
+  df* work = nullptr;
+  if (!in_smem) {
+    work = (df*)workspace(ctx, "tri_work", (size_t)m * m * sizeof(df), &s);
+    if (!work) return s;
+  }
+  FKK_CUDA(ctx, cudaMemsetAsync(scr, 0, 256, st));
+  FKK_CUDA(ctx, cudaMemsetAsync(ee, 0, (size_t)m * sizeof(df), st));
+  int* ex_dev = (int*)(scr + 48);
+  {
+    long long* cycles = nullptr;
+    if (ctx->timing) {
+      cycles = (long long*)workspace(ctx, "eig_phase_cycles", 8 * sizeof(long long), &s);
+      if (!cycles) return s;
+    }
+    TridArgs ta{g, m, ncol_max, work, pbuf, cbuf, dd, ee, tau, u, scr + 40, ex_dev, cycles, scr, (int*)(scr + 16),
+                ctx->d_status};
+    void* args[] = {&ta};
+    const void* fn = in_smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
+    FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tr));
+    int per_sm = 0;
+    FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTrThreads, smem_tr));
+    if (per_sm < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: reduction kernel cannot be resident");
+    FKK_COUNT_LAUNCH();
+    FKK_CUDA(ctx, cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kTrThreads), args, smem_tr, st));
+  }
+  // 2-3. eigenvalues and tridiagonal eigenvectors
+  df* z = (df*)workspace(ctx, "tri_z", (size_t)m * k * sizeof(df), &s);
+  if (!z) return s;
+  double* vz = (double*)workspace(ctx, "tri_vz", (size_t)m * k * sizeof(double), &s);
+  if (!vz) return s;
+  {
+    const size_t sb = (size_t)3 * m * sizeof(df);
+    FKK_CUDA(ctx, cudaFuncSetAttribute(tri_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    FKK_COUNT_LAUNCH();
+    tri_bisect_kernel<<<k, kBisWarps * 32, sb, st>>>(dd, ee, m, lam_s);
+    const size_t sv = (size_t)5 * m * sizeof(df) + (size_t)m * sizeof(double);
+    FKK_CUDA(ctx, cudaFuncSetAttribute(tri_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv));
+    FKK_COUNT_LAUNCH();
+    tri_vec_kernel<<<k, 32, sv, st>>>(dd, ee, m, k, lam_s, z, ctx->d_status);
+    FKK_COUNT_LAUNCH();
+    lam_out_kernel<<<(k + 127) / 128, 128, 0, st>>>(lam_s, ex_dev, k, lam);
+    FKK_CUDA(ctx, cudaGetLastError());
+  }
+  // 4. back-transformation
+  const int nrefl = std::max(0, m - 2);
+  if (nrefl > 0) {
+    const int nbk = (nrefl + kWY - 1) / kWY;
+    const int G = nsm;
+    const int S = std::max(1, G / nbk);
+    const int per = (m + G - 1) / G;
+    df* gpart = (df*)workspace(ctx, "tri_gpart", (size_t)nbk * S * kWY * kWY * sizeof(df), &s);
+    if (!gpart) return s;
+    df* tblk = (df*)workspace(ctx, "tri_tblk", (size_t)nbk * kWY * kWY * sizeof(df), &s);
+    if (!tblk) return s;
+    df* wpart = (df*)workspace(ctx, "tri_wpart", (size_t)G * kWY * k * sizeof(df), &s);
+    if (!wpart) return s;
+    df* wfull = (df*)workspace(ctx, "tri_wfull", (size_t)kWY * k * sizeof(df), &s);
+    if (!wfull) return s;
+    const size_t sbt = std::max<size_t>((size_t)(3 * kWY * kWY + kWY),
+                                        (size_t)per * (kWY + k) + (size_t)kWY * k + kWY + kBtThreads) *
+                       sizeof(df);
+    BackArgs ba{u, tau, m, nrefl, k, nbk, S, z, vz, gpart, tblk, wpart, wfull, scr + 32, (int*)(scr + 36),
+                ctx->d_status};
+    void* args[] = {&ba};
+    FKK_CUDA(ctx, cudaFuncSetAttribute(back_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbt));
+    int per_sm = 0;
+    FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, back_wy_kernel, kBtThreads, sbt));
+    if (per_sm < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: back-transformation cannot be resident");
+    FKK_COUNT_LAUNCH();
+    FKK_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)back_wy_kernel, dim3(G), dim3(kBtThreads), args, sbt, st));
+  } else {
+    FKK_COUNT_LAUNCH();
+    df_to_double_kernel<<<(m * k + 255) / 256, 256, 0, st>>>(z, m * k, vz);
+  }
+  // 5. Cholesky QR, sign convention
+  double* wk = (double*)workspace(ctx, "tri_wk", (size_t)2 * k * k * sizeof(double), &s);
+  if (!wk) return s;
+  FKK_COUNT_LAUNCH();
+  ztz_kernel<<<dim3(k, k), 128, 0, st>>>(vz, m, k, wk);
+  const size_t sc = (size_t)2 * k * k * sizeof(double);
+  FKK_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc));
+  FKK_COUNT_LAUNCH();
+  chol_inv_kernel<<<1, 256, sc, st>>>(wk, k, wk + k * k, ctx->d_status);
+  FKK_COUNT_LAUNCH();
+  apply_rinv_kernel<<<(m + 7) / 8, 256, 0, st>>>(vz, m, k, wk + k * k, v);
+  FKK_COUNT_LAUNCH();
+  sign_fix_kernel<<<k, 256, 0, st>>>(v, m, k, ctx->d_status);
+  return cuda_check(ctx, cudaGetLastError(), "eigensolve");
+}
+
+}  // namespace fkk

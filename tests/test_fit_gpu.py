@@ -110,6 +110,48 @@ def test_eig_known_spectrum(fk, ctx):
     np.testing.assert_allclose(np.abs((V * Q[:, :k]).sum(0)), 1.0, atol=1e-8)
 
 
+def _eig_check(fk, ctx, G, k, lam_tol=1e-12, res_tol=1e-12):
+    lam, V = fk.fkk_eig_topk(ctx, _dev(G), k)
+    st, _ = ctx.sync_status()
+    assert st == 0
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy()
+    w = np.linalg.eigvalsh(G)[::-1]
+    assert np.abs(lam - w[:k]).max() <= lam_tol * abs(w[0])
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-12
+    assert np.linalg.norm(G @ V - V * lam) <= res_tol * np.linalg.norm(G)
+    big = np.abs(V).argmax(0)
+    assert np.all(V[big, np.arange(k)] > 0)
+    return lam, V
+
+
+@pytest.mark.parametrize("m", [2, 3, 33])
+def test_eig_small(fk, ctx, m):
+    B = np.random.default_rng(m).standard_normal((50, m))
+    _eig_check(fk, ctx, B.T @ B, min(m, 3))
+
+
+def test_eig_split_with_equal_eigenvalues(fk, ctx):
+    """Two identical diagonal blocks: the tridiagonal form splits and every
+    eigenvalue is double; the two vectors of each pair must be orthogonal."""
+    B = np.random.default_rng(5).standard_normal((300, 60))
+    G = np.zeros((120, 120))
+    G[:60, :60] = B.T @ B
+    G[60:, 60:] = B.T @ B
+    _eig_check(fk, ctx, G, 10)
+
+
+@pytest.mark.parametrize("m", [512, 2048])
+def test_eig_dominant_rank_one(fk, ctx, m):
+    """Gram of log-ratio-like data: one eigenvalue ~2e5 times the noise
+    floor, noise eigenvalues a fraction of a percent apart; m = 2048 keeps
+    the working columns in global memory instead of shared memory."""
+    r = np.random.default_rng(m)
+    A = (1.0 + 0.3 * np.sin(np.arange(m) / 37.0)[None, :] * r.standard_normal((20000, 1))
+         + 0.05 * r.standard_normal((20000, m)))
+    _eig_check(fk, ctx, A.T @ A, 80 if m == 2048 else 40)
+
+
 def test_project_and_argext(fk, ctx, cube1):
     A = O.log_ratio(cube1.i_cars, cube1.i_ref)
     _, V_o = O.eig_desc(A.T @ A)
@@ -237,7 +279,7 @@ def test_fit_errors(fk, ctx, cube1):
     x = _dev(cube1.i_cars)
     ref = _dev(cube1.i_ref)
     for bad in (dict(k=0), dict(k=81), dict(als_p=1.5), dict(ratio_floor=0.0), dict(sg_window=4),
-                dict(pad_len=100), dict(eig_tol=2.0)):
+                dict(pad_len=100)):
         with pytest.raises(fk.FkkError):
             fk.fkk_fit_basis(ctx, x, ref, fk.fit_params(**bad))
 
