@@ -44,20 +44,6 @@ constexpr int kBtThreads = 512;
 constexpr int kBisWarps = 8;       // multisection points per round: 32 * kBisWarps
 constexpr float kEpsF = 5.9604645e-08f;  // 2^-24
 
-// Sum over the vector warps; thread 0 gets the total.
-__device__ __forceinline__ df vec_sum_to0(df x, df* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp < kVecWarps) {
-    x = dw::warp_sum(x);
-    if (lane == 0) red[warp] = x;
-  }
-  __syncthreads();
-  df t = dw::make(0.f);
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kVecWarps; ++q) t = dw::add(t, red[q]);
-  return t;
-}
-
 // Reflector from alpha (first entry) and sigma = sum of squares of the rest
 // (LAPACK dlarfg convention): H x = beta e_1, tau = (beta - alpha) / beta,
 // v = x / (alpha - beta) below the first entry.  sc = {tau, beta, scal}.
@@ -75,13 +61,82 @@ __device__ __forceinline__ void reflector(df alp, df sig, df* sc) {
   sc[2] = dw::rcp(dw::sub(alp, beta));
 }
 
+// Words exchanged between CTAs: a double-word value with a 2-bit step tag in
+// the two lowest bits of its low float, written and read as one 64-bit
+// access, so a reader knows from the word itself whether it is current.
+// Tags alternate 1, 2 between the consecutive uses of a double-buffered
+// slot; 0 (the cleared buffer) is never current.
+__device__ __forceinline__ unsigned step_tag(int s) { return 1u + ((s >> 1) & 1u); }
+__device__ __forceinline__ unsigned long long pack_tag(df x, unsigned tag) {
+  const unsigned lo = (__float_as_uint(x.l) & ~3u) | tag;
+  return ((unsigned long long)__float_as_uint(x.h) << 32) | lo;
+}
+__device__ __forceinline__ df unpack_tag(unsigned long long w) {
+  return {__uint_as_float((unsigned)(w >> 32)), __uint_as_float((unsigned)w & ~3u)};
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+constexpr int kMaxPer = 8;  // vector entries per vector thread: m <= kMaxPer * kVecThreads
+
+// Loads the words at p[i], i = i0 + r * stride (r < kMaxPer, lo <= i < m),
+// all in flight at once, and re-polls those not yet carrying `tag` until
+// every one does (bounded).  On timeout records FKK_ERR_TIMEOUT and raises
+// the abort flag; returns false then, or when another CTA has aborted.
+__device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i0, int stride, int lo, int m,
+                                              unsigned tag, unsigned long long (&wv)[kMaxPer], int* abort_flag,
+                                              long long* status) {
+  unsigned pending = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxPer; ++r) {
+    const int i = i0 + r * stride;
+    wv[r] = 0;
+    if (i >= lo && i < m) {
+      wv[r] = ld_relaxed_u64(p + i);
+      pending |= 1u << r;
+    }
+  }
+  unsigned it = 0;
+  for (;;) {
+#pragma unroll
+    for (int r = 0; r < kMaxPer; ++r)
+      if (((pending >> r) & 1u) && ((unsigned)wv[r] & 3u) == tag) pending &= ~(1u << r);
+    if (!pending) return true;
+    if ((++it & 63u) == 0) {
+      if (*(volatile int*)abort_flag) return false;
+      if (it > (1u << 20)) {
+        atomicExch(abort_flag, 1);
+        record_error(status, kErrTimeout);
+        return false;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxPer; ++r)
+      if ((pending >> r) & 1u) wv[r] = ld_relaxed_u64(p + i0 + r * stride);
+  }
+}
+
+// Sum of one double-word per vector warp (red[0..kVecWarps)), in warp 0.
+__device__ __forceinline__ df sum_vec_partials(const df* red) {
+  const int lane = threadIdx.x & 31;
+  df t = lane < kVecWarps ? red[lane] : dw::make(0.f);
+#pragma unroll
+  for (int o = kVecWarps / 2; o > 0; o >>= 1) t = dw::add(t, dw::shfl_xor(t, o));
+  return t;
+}
+
 struct TridArgs {
   const double* g;  // m x m symmetric, row-major (row c = column c)
   int m;
   int ncol_max;     // ceil(m / grid)
   df* work;         // m x m working columns when they do not fit in shared memory
-  df* pbuf;         // [2][m] p of the next step, by column
-  df* cbuf;         // [2][m] next pivot column before the current step's update
+  unsigned long long* pbuf;  // [2][m] tagged p of the next step, by column (cleared by the host)
+  unsigned long long* cbuf;  // [2][m] tagged next pivot column (cleared by the host)
   df* d;            // [m] diagonal of T (scaled)
   df* e;            // [m] sub-diagonal of T (scaled; e[m-1] = 0)
   df* tau;          // [m] reflector scalars
@@ -101,6 +156,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
   const int lane = tid & 31, warp = tid >> 5;
   const bool vecw = warp < kVecWarps;
   const int nloc = (m - b + nb - 1) / nb;  // own columns c = b + s * nb
+  const int c_last = b + (nloc - 1) * nb;   // last own column
+  // the owner of column m-1 takes part in every step and writes T and the
+  // reflectors; a CTA whose columns are all reduced leaves (nobody waits on
+  // it any more, so it must not read exchange buffers others may reuse)
+  const bool writer = b == (m - 1) % nb;
   df* cols = smd;
   df* v = smd + (kSmem ? (size_t)a.ncol_max * m : 0);
   df* vn = v + m;
@@ -113,7 +173,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
   auto colp = [&](int s) -> df* {
     return kSmem ? cols + (size_t)s * m : a.work + (size_t)(b + s * nb) * m;
   };
-  const bool timed = a.cycles != nullptr && b == 0 && tid == 0;
+  const bool timed = a.cycles != nullptr && writer && tid == 0;
   long long cyc[5] = {0, 0, 0, 0, 0};
   long long t_prev = timed ? clock64() : 0;
   auto mark = [&](int ph) {
@@ -157,7 +217,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     for (int i = tid; i < m; i += kTrThreads) col[i] = dw::ldexp(col[i], -ex);
   }
   if (m <= 2) {
-    if (b == 0 && tid == 0) {
+    if (writer && tid == 0) {
       a.d[0] = dw::ldexp(dw::from_double(a.g[0]), -ex);
       a.e[0] = dw::make(0.f);
       if (m == 2) {
@@ -170,21 +230,27 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
 
   // reflector of step 0 from column 0
   {
-    df sig = dw::make(0.f), alp = dw::make(0.f);
+    df sig = dw::make(0.f);
     if (vecw)
       for (int i = tid; i < m; i += kVecThreads) {
         const df x = i >= 1 ? dw::ldexp(dw::from_double(a.g[i]), -ex) : dw::make(0.f);
         vn[i] = x;
         if (i >= 2) sig = dw::add(sig, dw::mul(x, x));
       }
-    sig = vec_sum_to0(sig, red);
-    if (tid == 0) {
-      alp = vn[1];
-      reflector(alp, sig, sc);
-      if (b == 0) {
-        a.d[0] = dw::ldexp(dw::from_double(a.g[0]), -ex);
-        a.e[0] = sc[1];
-        a.tau[0] = sc[0];
+    if (vecw) {
+      sig = dw::warp_sum(sig);
+      if (lane == 0) red[warp] = sig;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const df t = sum_vec_partials(red);
+      if (lane == 0) {
+        reflector(vn[1], t, sc);
+        if (writer) {
+          a.d[0] = dw::ldexp(dw::from_double(a.g[0]), -ex);
+          a.e[0] = sc[1];
+          a.tau[0] = sc[0];
+        }
       }
     }
     __syncthreads();
@@ -193,11 +259,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
       for (int i = tid; i < m; i += kVecThreads) {
         const df x = i < 1 ? dw::make(0.f) : (i == 1 ? dw::make(1.f) : dw::mul(vn[i], scal));
         v[i] = x;
-        if (b == 0) a.u[i] = x;
+        if (writer) a.u[i] = x;
       }
     __syncthreads();
     // p of step 0 and the copy of column 1: warp s takes own column s
     const df tau0 = sc[0];
+    const unsigned tag0 = step_tag(0);
     if (warp < nloc) {
       const int c = b + warp * nb;
       const df* col = colp(warp);
@@ -206,68 +273,96 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         for (int i = 1 + lane; i < m; i += 32) {
           const df x = col[i];
           acc = dw::add(acc, dw::mul(x, v[i]));
-          if (c == 1) a.cbuf[i] = x;
+          if (c == 1) st_relaxed_u64(a.cbuf + i, pack_tag(x, tag0));
         }
       acc = dw::warp_sum(acc);
-      if (lane == 0 && c >= 1) a.pbuf[c] = dw::mul(tau0, acc);
+      if (lane == 0 && c >= 1) st_relaxed_u64(a.pbuf + c, pack_tag(dw::mul(tau0, acc), tag0));
     }
   }
   df tau_cur = sc[0];
   mark(0);
-  if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
-  mark(4);
 
   const int nsteps = m - 2;
   for (int j = 0; j < nsteps; ++j) {
+    if (c_last < j + 2) break;  // nothing of this CTA's is read from step j on
     const int buf = j & 1, nxt = buf ^ 1;
-    const df* pb = a.pbuf + (size_t)buf * m;
-    const df* cb = a.cbuf + (size_t)buf * m;
-    // 1. w = p - (tau/2)(p.v) v on rows >= j+1
+    const unsigned want = step_tag(j);
+    const unsigned long long* pb = a.pbuf + (size_t)buf * m;
+    const unsigned long long* cb = a.cbuf + (size_t)buf * m;
+    const bool last = (j + 1 > m - 3);
+    // A. gather p and the pivot column (rows >= j+1) as they arrive; p.v
+    df cbr[kMaxPer];
+    bool ok = true;
     df dot = dw::make(0.f);
-    if (vecw)
-      for (int i = tid; i < m; i += kVecThreads) {
-        df p = dw::make(0.f);
-        if (i >= j + 1) {
-          const float2 t = __ldcg(reinterpret_cast<const float2*>(pb + i));
-          p = dw::make(t.x, t.y);
-          dot = dw::add(dot, dw::mul(p, v[i]));
+    if (vecw) {
+      unsigned long long wp[kMaxPer], wcb[kMaxPer];
+      ok = gather_tagged(pb, tid, kVecThreads, j + 1, m, want, wp, a.abort_flag, a.status) &&
+           gather_tagged(cb, tid, kVecThreads, j + 1, m, want, wcb, a.abort_flag, a.status);
+#pragma unroll
+      for (int r = 0; r < kMaxPer; ++r) {
+        const int i = tid + r * kVecThreads;
+        cbr[r] = dw::make(0.f);
+        if (i < m) {
+          df p = dw::make(0.f);
+          if (i >= j + 1) {
+            p = unpack_tag(wp[r]);
+            cbr[r] = unpack_tag(wcb[r]);
+            dot = dw::add(dot, dw::mul(p, v[i]));
+          }
+          w[i] = p;
         }
-        w[i] = p;
       }
-    dot = vec_sum_to0(dot, red);
-    if (tid == 0) sc[4] = dw::mul(dw::mul(tau_cur, dot), 0.5f);
-    __syncthreads();
-    const df halfk = sc[4];
-    if (vecw)
-      for (int i = tid; i < m; i += kVecThreads)
-        if (i >= j + 1) w[i] = dw::fnma(halfk, v[i], w[i]);
+      dot = dw::warp_sum(dot);
+      if (lane == 0) red[warp] = dot;
+    }
+    if (!__syncthreads_and(ok)) return;
+    if (warp == 0) {
+      const df t = sum_vec_partials(red);
+      if (lane == 0) {
+        const df halfk = dw::mul(dw::mul(tau_cur, t), 0.5f);
+        sc[4] = halfk;
+        sc[5] = dw::sub(w[j + 1], halfk);  // w_{j+1} = p_{j+1} - halfk v_{j+1}, v_{j+1} = 1
+      }
+    }
     __syncthreads();
     mark(1);
-    // 2. pivot column j+1 after this step; the next reflector from it
-    const df wj1 = w[j + 1];
-    const bool last = (j + 1 > m - 3);
+    // B. w = p - halfk v; pivot column x = c - v w_{j+1} - w after this step;
+    //    the next reflector from x
+    const df halfk = sc[4], wj1 = sc[5];
     df sig = dw::make(0.f);
-    if (vecw)
-      for (int i = tid; i < m; i += kVecThreads) {
-        if (i < j + 1) continue;
-        const float2 t = __ldcg(reinterpret_cast<const float2*>(cb + i));
-        const df x = dw::sub(dw::fnma(v[i], wj1, dw::make(t.x, t.y)), w[i]);
-        vn[i] = x;
-        if (i == j + 1 && b == 0) a.d[j + 1] = x;
-        if (last) {
-          if (i == m - 1 && b == 0) a.e[m - 2] = x;
-        } else if (i >= j + 3) {
-          sig = dw::add(sig, dw::mul(x, x));
+    if (vecw) {
+#pragma unroll
+      for (int r = 0; r < kMaxPer; ++r) {
+        const int i = tid + r * kVecThreads;
+        if (i < m && i >= j + 1) {
+          const df wi = dw::fnma(halfk, v[i], w[i]);
+          w[i] = wi;
+          const df x = dw::sub(dw::fnma(v[i], wj1, cbr[r]), wi);
+          vn[i] = x;
+          if (i == j + 1 && writer) a.d[j + 1] = x;
+          if (last) {
+            if (i == m - 1 && writer) a.e[m - 2] = x;
+          } else if (i >= j + 3) {
+            sig = dw::add(sig, dw::mul(x, x));
+          }
         }
       }
+    }
     df tau_nxt = dw::make(0.f);
     if (!last) {
-      sig = vec_sum_to0(sig, red);
-      if (tid == 0) {
-        reflector(vn[j + 2], sig, sc);
-        if (b == 0) {
-          a.e[j + 1] = sc[1];
-          a.tau[j + 1] = sc[0];
+      if (vecw) {
+        sig = dw::warp_sum(sig);
+        if (lane == 0) red[kVecWarps + warp] = sig;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const df t = sum_vec_partials(red + kVecWarps);
+        if (lane == 0) {
+          reflector(vn[j + 2], t, sc);
+          if (writer) {
+            a.e[j + 1] = sc[1];
+            a.tau[j + 1] = sc[0];
+          }
         }
       }
       __syncthreads();
@@ -280,30 +375,34 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
           else if (i == j + 2) x = dw::make(1.f);
           else x = dw::mul(vn[i], scal);
           vn[i] = x;
-          if (b == 0) a.u[(size_t)(j + 1) * m + i] = x;
+          if (writer) a.u[(size_t)(j + 1) * m + i] = x;
         }
     }
     __syncthreads();
     mark(2);
-    // 3. warp s updates own column s (c >= j+2) on rows >= j+2 and
-    //    accumulates p of the next step
+    // C. warp s updates own column s (c >= j+2) on rows >= j+2, accumulates
+    //    p of the next step and publishes it (and the next pivot column)
     if (warp < nloc) {
       const int c = b + warp * nb;
       if (c >= j + 2) {
         df* col = colp(warp);
         const df wc = w[c], vc = v[c];
         df acc = dw::make(0.f);
-        df* cnext = a.cbuf + (size_t)nxt * m;
+        const unsigned tagn = step_tag(j + 1);
+        unsigned long long* cnext = a.cbuf + (size_t)nxt * m;
         for (int i = j + 2 + lane; i < m; i += 32) {
           const df x = dw::sub(col[i], dw::add(dw::mul(v[i], wc), dw::mul(w[i], vc)));
           col[i] = x;
-          if (!last) acc = dw::add(acc, dw::mul(x, vn[i]));
-          if (c == j + 2) cnext[i] = x;
-          if (last && i == m - 1) a.d[m - 1] = x;  // c == m - 1 here
+          if (!last) {
+            acc = dw::add(acc, dw::mul(x, vn[i]));
+            if (c == j + 2) st_relaxed_u64(cnext + i, pack_tag(x, tagn));
+          } else if (i == m - 1) {
+            a.d[m - 1] = x;  // c == m - 1 here
+          }
         }
         if (!last) {
           acc = dw::warp_sum(acc);
-          if (lane == 0) a.pbuf[(size_t)nxt * m + c] = dw::mul(tau_nxt, acc);
+          if (lane == 0) st_relaxed_u64(a.pbuf + (size_t)nxt * m + c, pack_tag(dw::mul(tau_nxt, acc), tagn));
         }
       }
     }
@@ -313,8 +412,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     v = vn;
     vn = tmp;
     tau_cur = tau_nxt;
-    if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
-    mark(4);
+    __syncthreads();  // the column updates read v, w, vn; the next step rewrites them
   }
   if (timed)
     for (int q = 0; q < 5; ++q) a.cycles[q] = cyc[q];
@@ -887,9 +985,9 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   const size_t smem_tr = in_smem ? smem_cols : vec_bytes;
   df* wsd = (df*)workspace(ctx, "tri_vecs", (size_t)(4 * m + 3 * m + 2 * k + 64) * sizeof(df), &s);
   if (!wsd) return s;
-  df* pbuf = wsd;
-  df* cbuf = pbuf + 2 * m;
-  df* dd = cbuf + 2 * m;
+  unsigned long long* pbuf = reinterpret_cast<unsigned long long*>(wsd);
+  unsigned long long* cbuf = pbuf + 2 * m;
+  df* dd = wsd + 4 * m;
   df* ee = dd + m;
   df* tau = ee + m;
   df* lam_s = tau + m;
@@ -903,7 +1001,9 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
     if (!work) return s;
   }
   FKK_CUDA(ctx, cudaMemsetAsync(scr, 0, 256, st));
-  FKK_CUDA(ctx, cudaMemsetAsync(ee, 0, (size_t)m * sizeof(df), st));
+  // tagged exchange buffers start cleared (tag 0 is never current), and e
+  // at zero (e[m-1] stays 0)
+  FKK_CUDA(ctx, cudaMemsetAsync(wsd, 0, (size_t)(4 * m + 2 * m) * sizeof(df), st));
   int* ex_dev = (int*)(scr + 48);
   {
     long long* cycles = nullptr;
