@@ -59,6 +59,11 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
 fkk_status launch_project(fkk_ctx* ctx, const DtLayout& L, const double* w, const double* f, int k, float* p,
                           int64_t* qmax, int64_t* qmin, cudaStream_t st);
 
+// Same on the tensor cores (bf16 hi/lo operands, four products); cand, when
+// not null, receives per 128-row tile and column (max, argmax, min, argmin).
+fkk_status launch_project_tc(fkk_ctx* ctx, const DtLayout& L, const double* w, const double* f, int k, float* p,
+                             float4* cand, cudaStream_t st);
+
 // P = A W from the raw cube (for new data): A = f * 1/2 ln(max(I/I_ref, floor)).
 fkk_status launch_project_raw(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
                               const float* i_ref, float floor_, const double* w, const double* f, int k,

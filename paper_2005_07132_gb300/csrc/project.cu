@@ -203,19 +203,13 @@ fkk_status dispatch_project(fkk_ctx* ctx, ProjArgs& a, unsigned grid, cudaStream
 fkk_status launch_project(fkk_ctx* ctx, const DtLayout& L, const double* w, const double* f, int k, float* p,
                           int64_t* qmax, int64_t* qmin, cudaStream_t st) {
   fkk_status s;
-  float* wf = (float*)workspace(ctx, "proj_wf", (size_t)L.m * k * 4, &s);
-  if (!wf) return s;
-  float* off = (float*)workspace(ctx, "proj_off", (size_t)k * 4, &s);
-  if (!off) return s;
-  const unsigned grid = (unsigned)((L.n + kRows - 1) / kRows);
+  const unsigned grid = (unsigned)((L.n + kRows - 1) / kRows);  // 128-row tiles
   float4* cand = nullptr;
   if (qmax) {
     cand = (float4*)workspace(ctx, "proj_cand", (size_t)grid * k * sizeof(float4), &s);
     if (!cand) return s;
   }
-  FKK_COUNT_LAUNCH(); prep_w_kernel<<<k, 256, 0, st>>>(w, f, L.c, L.m, k, wf, off);
-  ProjArgs a{L.dt_hi, L.dt_lo, L.np, nullptr, 0, nullptr, 0.f, L.n, L.m, k, wf, off, p, cand, ctx->d_status};
-  FKK_TRY(dispatch_project<false>(ctx, a, grid, st));
+  FKK_TRY(launch_project_tc(ctx, L, w, f, k, p, cand, st));
   if (qmax) {
     FKK_COUNT_LAUNCH(); argext_reduce_kernel<<<k, 256, 0, st>>>(cand, (int)grid, k, qmax, qmin);
     FKK_CUDA(ctx, cudaGetLastError());
