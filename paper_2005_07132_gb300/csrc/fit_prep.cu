@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   const int j0 = blockIdx.y * 64;
   const int j = j0 + tx;
   const bool jvalid = j < p.m;
-  const float r = jvalid ? p.i_ref[j] : 1.f;
+  const float rinv = jvalid ? 1.f / p.i_ref[j] : 1.f;
   const float cj = jvalid ? p.c[j] : 0.f;
   const int64_t nrt = p.np / 64;
   double sum_d = 0.0, sum_i = 0.0;
@@ -45,13 +45,21 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   for (int64_t rt = blockIdx.x; rt < nrt; rt += gridDim.x) {
     const int64_t n0 = rt * 64;
     float td = 0.f, ti = 0.f;
-#pragma unroll 4
-    for (int rr = ty; rr < 64; rr += 4) {
-      int64_t n = n0 + rr;
+    // all 16 loads of this thread in flight before any arithmetic
+    float vals[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int64_t n = n0 + ty + 4 * u;
+      vals[u] = (jvalid && n < p.n) ? __ldcs(p.i_cars + n * p.ld + j) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int rr = ty + 4 * u;
+      const int64_t n = n0 + rr;
       float d = 0.f;
       if (jvalid && n < p.n) {
-        float v = p.i_cars[n * p.ld + j];
-        float x = v / r;
+        const float v = vals[u];
+        float x = v * rinv;
         if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
         d = 0.5f * logf(x) - cj;
         td += d;
