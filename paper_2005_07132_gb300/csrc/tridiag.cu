@@ -40,8 +40,7 @@ constexpr int kVecWarps = 8;  // warps that run the length-m vector phases
 constexpr int kVecThreads = kVecWarps * 32;
 constexpr int kMaxLoc = kTrWarps;  // columns per CTA (one warp each): m <= kMaxLoc * grid
 constexpr int kWY = 32;            // reflectors per block in the back-transformation
-constexpr int kBtThreads = 512;
-constexpr int kBisWarps = 8;       // multisection points per round: 32 * kBisWarps
+constexpr int kBisWarps = 4;       // multisection points per round: 32 * kBisWarps
 constexpr float kEpsF = 5.9604645e-08f;  // 2^-24
 
 // Reflector from alpha (first entry) and sigma = sum of squares of the rest
@@ -474,6 +473,15 @@ __device__ TriBounds load_tri(const df* __restrict__ d, const df* __restrict__ e
   return t;
 }
 
+// Power of two bringing the larger of two floats' exponents to zero, when
+// that exponent has left [-32, 32] (else 1): exact rescaling by exponent bits.
+__device__ __forceinline__ float rescale_factor(float a, float b) {
+  const int ea = (__float_as_int(a) >> 23) & 0xff, eb = (__float_as_int(b) >> 23) & 0xff;
+  const int e = max(ea, eb);
+  if (e > 127 + 32 || e < 127 - 32) return __int_as_float(max(1, min(254, 254 - e)) << 23);
+  return 1.f;
+}
+
 // Number of eigenvalues of Ts below x: sign changes of the leading principal
 // minors of Ts - x I (three-term recurrence; an exact zero minor counts as a
 // tiny negative pivot).  The minors can shrink by the ratio of the smallest
@@ -484,26 +492,105 @@ __device__ __forceinline__ int sturm_count(const df* ds, const df* eb, int m, df
   df p2 = dw::make(1.f);
   df p1 = dw::sub(ds[0], x);
   if (p1.h == 0.f) p1 = dw::make(-0x1p-60f);
-  int cnt = dw::lt0(p1);
+  int cnt = p1.h < 0.f;
   for (int i = 1; i < m; ++i) {
     df p = dw::sub(dw::mul(dw::sub(ds[i], x), p1), dw::mul(eb[i], p2));
     if (p.h == 0.f) p = dw::mul(p1, -0x1p-60f);
-    cnt += dw::lt0(p) != dw::lt0(p1);
+    cnt += (p.h < 0.f) != (p1.h < 0.f);
     p2 = p1;
     p1 = p;
-    const float mxp = fmaxf(fabsf(p1.h), fabsf(p2.h));
-    if (mxp > 0x1p32f || mxp < 0x1p-32f) {
-      const int sh = ilogbf(mxp);
-      p1 = dw::ldexp(p1, -sh);
-      p2 = dw::ldexp(p2, -sh);
+    const float f = rescale_factor(p1.h, p2.h);
+    if (f != 1.f) {
+      p1 = dw::mul(p1, f);
+      p2 = dw::mul(p2, f);
     }
   }
   return cnt;
 }
 
-// One CTA per eigenvalue: rank r = m-1-c (c = 0 the largest).  Each round
-// evaluates 32 * kBisWarps interior points of the bracket [lo, hi]
-// (N(lo) <= r < N(hi)) and keeps the sub-interval where the count crosses r.
+// Two counts at once (independent recurrences interleaved, to hide the
+// dependent latency of each).
+__device__ __forceinline__ void sturm_count2(const df* ds, const df* eb, int m, df x, df y, int& nx, int& ny) {
+  df p2 = dw::make(1.f), q2 = p2;
+  df p1 = dw::sub(ds[0], x), q1 = dw::sub(ds[0], y);
+  if (p1.h == 0.f) p1 = dw::make(-0x1p-60f);
+  if (q1.h == 0.f) q1 = dw::make(-0x1p-60f);
+  int cx = p1.h < 0.f, cy = q1.h < 0.f;
+  for (int i = 1; i < m; ++i) {
+    const df di = ds[i], ei = eb[i];
+    df p = dw::sub(dw::mul(dw::sub(di, x), p1), dw::mul(ei, p2));
+    df q = dw::sub(dw::mul(dw::sub(di, y), q1), dw::mul(ei, q2));
+    // branch-free: an exact zero becomes a tiny negative multiple of the
+    // previous minor; the rescale factor is 1 when none is needed (exact)
+    const bool pz = p.h == 0.f, qz = q.h == 0.f;
+    p.h = pz ? -0x1p-60f * p1.h : p.h;
+    p.l = pz ? 0.f : p.l;
+    q.h = qz ? -0x1p-60f * q1.h : q.h;
+    q.l = qz ? 0.f : q.l;
+    cx += (p.h < 0.f) != (p1.h < 0.f);
+    cy += (q.h < 0.f) != (q1.h < 0.f);
+    const float f = rescale_factor(p.h, p1.h), g = rescale_factor(q.h, q1.h);
+    p2 = {p1.h * f, p1.l * f};
+    p1 = {p.h * f, p.l * f};
+    q2 = {q1.h * g, q1.l * g};
+    q1 = {q.h * g, q.l * g};
+  }
+  nx = cx;
+  ny = cy;
+}
+
+// The same count in plain fp32 on the leading words: exact for a matrix
+// within a few float roundings of Ts, used to bracket before the
+// double-word rounds.
+__device__ __forceinline__ int sturm_count_f32(const df* ds, const df* eb, int m, float x) {
+  float p2 = 1.f, p1 = ds[0].h - x;
+  if (p1 == 0.f) p1 = -0x1p-60f;
+  int cnt = p1 < 0.f;
+  for (int i = 1; i < m; ++i) {
+    float p = fmaf(ds[i].h - x, p1, -eb[i].h * p2);
+    if (p == 0.f) p = -0x1p-60f * p1;
+    cnt += (p < 0.f) != (p1 < 0.f);
+    p2 = p1;
+    p1 = p;
+    const float f = rescale_factor(p1, p2);
+    p1 *= f;
+    p2 *= f;
+  }
+  return cnt;
+}
+
+// First of the 2 x blockDim points (thread t holds points 2t and 2t + 1)
+// whose count exceeds r; 2 x blockDim if none.
+__device__ __forceinline__ int first_above2(int n0, int n1, int r, int* first_s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // bit pattern over the warp's 64 points, in point order
+  const unsigned a0 = __ballot_sync(0xffffffffu, n0 > r), a1 = __ballot_sync(0xffffffffu, n1 > r);
+  if (lane == 0) {
+    int f = 64;
+    const unsigned any = a0 | a1;
+    if (any) {
+      const int t = __ffs(any) - 1;  // first thread with a crossing
+      f = 2 * t + (((a0 >> t) & 1u) ? 0 : 1);
+    }
+    first_s[warp] = f;
+  }
+  __syncthreads();
+  int first = 2 * (int)blockDim.x;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+    if (first_s[q] < 64) {
+      first = q * 64 + first_s[q];
+      break;
+    }
+  return first;
+}
+
+// One CTA per eigenvalue: rank r = m-1-c (c = 0 the largest).  Rounds of
+// multisection evaluate P = 2 x blockDim points of the bracket [lo, hi]
+// (N(lo) <= r < N(hi)) and keep the sub-interval where the count crosses r:
+// first in fp32 down to the float resolution, then, from that bracket
+// widened by the fp32 count's error bound, in double-word.  The first
+// double-word round includes the bracket ends and falls back to the
+// Gershgorin interval if they do not bracket rank r.
 __global__ void __launch_bounds__(kBisWarps * 32) tri_bisect_kernel(const df* __restrict__ d,
                                                                     const df* __restrict__ e, int m,
                                                                     df* __restrict__ lam) {
@@ -514,31 +601,62 @@ __global__ void __launch_bounds__(kBisWarps * 32) tri_bisect_kernel(const df* __
   __shared__ float redf[64];
   __shared__ int first_s[kBisWarps];
   __shared__ df lohi[2];
-  const int P = kBisWarps * 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float flh[2];
+  const int P = 2 * kBisWarps * 32;
+  const int tid = threadIdx.x;
   const int c = blockIdx.x;
   const int r = m - 1 - c;
   const TriBounds t = load_tri(d, e, m, ds, es, eb, redf);
-  df lo = dw::make(t.gl), hi = dw::make(t.gu);
-  const float tol = 8.f * kEpsF * kEpsF * fmaxf(fabsf(t.gl), fabsf(t.gu));
+  const float gmax = fmaxf(fabsf(t.gl), fabsf(t.gu));
+  // fp32 rounds
+  float flo = t.gl, fhi = t.gu;
+  for (int round = 0; round < 8 && fhi - flo > 64.f * kEpsF * gmax; ++round) {
+    const float x0 = flo + (fhi - flo) * ((float)(2 * tid + 1) / (float)(P + 1));
+    const float x1 = flo + (fhi - flo) * ((float)(2 * tid + 2) / (float)(P + 1));
+    const int n0 = sturm_count_f32(ds, eb, m, x0), n1 = sturm_count_f32(ds, eb, m, x1);
+    const int first = first_above2(n0, n1, r, first_s);
+    if (first - 1 == 2 * tid) flh[0] = x0;
+    if (first - 1 == 2 * tid + 1) flh[0] = x1;
+    if (first == 2 * tid) flh[1] = x0;
+    if (first == 2 * tid + 1) flh[1] = x1;
+    __syncthreads();
+    if (first > 0) flo = flh[0];
+    if (first < P) fhi = flh[1];
+    __syncthreads();
+  }
+  // double-word rounds
+  const float widen = 64.f * kEpsF * gmax;
+  df lo = dw::make(flo - widen), hi = dw::make(fhi + widen);
+  const float tol = 8.f * kEpsF * kEpsF * gmax;
+  bool first_round = true;
   for (int round = 0; round < 24; ++round) {
     const df wid = dw::sub(hi, lo);
     if (wid.h <= tol) break;
-    const float f = (float)(tid + 1) / (float)(P + 1);
-    const df x = dw::add(lo, dw::mul(wid, f));
-    const int n = sturm_count(ds, eb, m, x);
-    const unsigned above = __ballot_sync(0xffffffffu, n > r);
-    if (lane == 0) first_s[warp] = above ? __ffs(above) - 1 : 32;
-    __syncthreads();
-    // first point (in block order) whose count exceeds r
-    int first = P;
-    for (int q = 0; q < kBisWarps; ++q)
-      if (first_s[q] < 32) {
-        first = q * 32 + first_s[q];
-        break;
-      }
-    if (tid == first - 1) lohi[0] = x;
-    if (tid == first) lohi[1] = x;
+    df x0, x1;
+    if (first_round) {  // ends included
+      x0 = dw::add(lo, dw::mul(wid, (float)(2 * tid) / (float)(P - 1)));
+      x1 = dw::add(lo, dw::mul(wid, (float)(2 * tid + 1) / (float)(P - 1)));
+    } else {
+      x0 = dw::add(lo, dw::mul(wid, (float)(2 * tid + 1) / (float)(P + 1)));
+      x1 = dw::add(lo, dw::mul(wid, (float)(2 * tid + 2) / (float)(P + 1)));
+    }
+    int n0, n1;
+    sturm_count2(ds, eb, m, x0, x1, n0, n1);
+    const int first = first_above2(n0, n1, r, first_s);
+    if (first_round && (first == 0 || first == P)) {
+      // the widened fp32 bracket does not hold rank r: start over from the
+      // Gershgorin interval
+      __syncthreads();
+      lo = dw::make(t.gl);
+      hi = dw::make(t.gu);
+      first_round = false;
+      continue;
+    }
+    first_round = false;
+    if (first - 1 == 2 * tid) lohi[0] = x0;
+    if (first - 1 == 2 * tid + 1) lohi[0] = x1;
+    if (first == 2 * tid) lohi[1] = x0;
+    if (first == 2 * tid + 1) lohi[1] = x1;
     __syncthreads();
     if (first > 0) lo = lohi[0];
     if (first < P) hi = lohi[1];
@@ -562,7 +680,8 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
   df* eb = es + m;
   df* dp = eb + m;
   df* dm = dp + m;
-  double* z = reinterpret_cast<double*>(dm + m);
+  df* z = dm + m;
+  int* ez = reinterpret_cast<int*>(z + m);  // z_i = z[i] * 2^ez[i]
   __shared__ float redf[64];
   const int lane = threadIdx.x;
   const int c = blockIdx.x;
@@ -647,201 +766,266 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
     if (lane == 0) record_error(status, kErrNotConverged);
     r = 0;
   }
-  // ratios (in place), then the two product chains in fp64: a pivot at the
-  // floor gives a ratio near 2^90, beyond what the float exponent of a
-  // double-word can carry through a product chain
+  // ratios (in place), then the two product chains; a pivot at the floor
+  // gives a ratio near 2^90, so each chain keeps its running value in
+  // [2^-40, 2^40] and carries the power of two separately
   for (int i = lane; i < m; i += 32) {
     if (i < r) dp[i] = dw::neg(dw::div(es[i], dp[i]));
     else if (i > r) dm[i] = dw::neg(dw::div(es[i - 1], dm[i]));
   }
   __syncwarp();
+  auto chain_step = [&](df ratio, df& x, int& ex) {
+    x = dw::mul(ratio, x);
+    const int be = ((__float_as_int(x.h) >> 23) & 0xff) - 127;
+    if (x.h == 0.f) {
+      ex = -100000;
+    } else if (be > 40 || be < -40) {
+      x = dw::mul(x, __int_as_float((127 - be) << 23));
+      ex += be;
+    }
+  };
   if (lane == 0) {
-    z[r] = 1.0;
-    double x = 1.0;
+    z[r] = dw::make(1.f);
+    ez[r] = 0;
+    df x = dw::make(1.f);
+    int ex = 0;
     for (int i = r - 1; i >= 0; --i) {
-      x = fabs(x) < 1e-280 ? 0.0 : dw::to_double(dp[i]) * x;
-      z[i] = x;
+      if (ex > -100000) chain_step(dp[i], x, ex);
+      z[i] = ex > -100000 ? x : dw::make(0.f);
+      ez[i] = ex;
     }
   } else if (lane == 1) {
-    double x = 1.0;
+    df x = dw::make(1.f);
+    int ex = 0;
     for (int i = r + 1; i < m; ++i) {
-      x = fabs(x) < 1e-280 ? 0.0 : dw::to_double(dm[i]) * x;
-      z[i] = x;
+      if (ex > -100000) chain_step(dm[i], x, ex);
+      z[i] = ex > -100000 ? x : dw::make(0.f);
+      ez[i] = ex;
     }
   }
   __syncwarp();
-  double nrm = 0.0;
-  for (int i = lane; i < m; i += 32) nrm = fma(z[i], z[i], nrm);
-  nrm = warp_sum(nrm);
-  if (!(nrm >= 1.0 && nrm < 1e300)) {  // z[r] = 1, so nrm >= 1 unless something overflowed
+  // common scale: the largest power of two carried, entries far below it vanish
+  int emax = -1000000;
+  for (int i = lane; i < m; i += 32)
+    if (z[i].h != 0.f) emax = max(emax, ez[i] + (((__float_as_int(z[i].h) >> 23) & 0xff) - 127));
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  df nrm = dw::make(0.f);
+  for (int i = lane; i < m; i += 32) {
+    const int sh = ez[i] - emax;
+    const df zi = (z[i].h == 0.f || sh < -120) ? dw::make(0.f) : dw::ldexp(z[i], sh);
+    z[i] = zi;
+    nrm = dw::add(nrm, dw::mul(zi, zi));
+  }
+  nrm = dw::warp_sum(nrm);
+  if (!(nrm.h >= 1e-6f && nrm.h < 1e6f)) {  // the largest entry is in [1, 2): nrm >= 1
     if (lane == 0) record_error(status, kErrNotConverged);
     for (int i = lane; i < m; i += 32) z_out[(size_t)i * k + c] = dw::make(i == r ? 1.f : 0.f);
     return;
   }
-  const double inv = 1.0 / sqrt(nrm);
-  for (int i = lane; i < m; i += 32) z_out[(size_t)i * k + c] = dw::from_double(z[i] * inv);
+  const df inv = dw::rcp(dw::sqrt(nrm));
+  for (int i = lane; i < m; i += 32) z_out[(size_t)i * k + c] = dw::mul(z[i], inv);
 }
 
 // ---------------------------------------------------------------------------
-// Back-transformation V = Q Z, Q = H_0 H_1 ... H_{m-3}, blocks of 32
-// reflectors B_b = I - Y_b T_b Y_b^T (T_b upper triangular), applied from the
-// last block to the first.  Cooperative: rows are split evenly over the CTAs.
-// The result is written in fp64.
+// Back-transformation V = Q Z, Q = H_0 H_1 ... H_{m-3}, in blocks of 32
+// reflectors B_b = I - Y_b T_b Y_b^T (T_b upper triangular) applied from the
+// last block to the first.  wy_gram_kernel forms slices of Y_b^T Y_b,
+// wy_t_kernel the factors T_b, and wy_apply_kernel applies all blocks to one
+// column of Z per CTA (the columns are independent, so no grid-wide step).
 
-struct BackArgs {
-  const df* u;    // [m][m] reflector rows
-  const df* tau;  // [nrefl]
-  int m, nrefl, k, nbk, S;
-  df* z;          // [m][k] in / out
-  double* v;      // [m][k] result
-  df* gpart;      // [nbk][S][32 * 32]
-  df* tblk;       // [nbk][32 * 32]
-  df* wpart;      // [grid][32 * k]
-  df* wfull;      // [32 * k]
-  unsigned* bar;
-  int* abort_flag;
-  long long* status;
-};
+constexpr int kWyThreads = 256;
 
-__global__ void __launch_bounds__(kBtThreads, 1) back_wy_kernel(BackArgs a) {
+// gpart[b][part] = (Y_b^T Y_b restricted to a slice of rows), upper triangle.
+__global__ void __launch_bounds__(kWyThreads) wy_gram_kernel(const df* __restrict__ u, int m, int nrefl, int S,
+                                                             df* __restrict__ gpart) {
+  __shared__ df ys[32 * kWY];
+  const int b = blockIdx.x, part = blockIdx.y, tid = threadIdx.x;
+  const int j0 = b * kWY, nr = min(kWY, nrefl - j0);
+  const int rbeg = j0 + 1, rows = m - rbeg;
+  const int per = (rows + S - 1) / S;
+  const int i0 = rbeg + part * per, i1 = min(m, i0 + per);
+  constexpr int np = kWY * (kWY + 1) / 2;
+  constexpr int kPer = (np + kWyThreads - 1) / kWyThreads;
+  int pp[kPer], qq[kPer];
+  df acc[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int idx = tid + t * kWyThreads;
+    pp[t] = -1;
+    qq[t] = -1;
+    acc[t] = dw::make(0.f);
+    if (idx < np) {
+      int pr = 0, rem = idx;
+      while (rem >= kWY - pr) { rem -= kWY - pr; ++pr; }
+      pp[t] = pr;
+      qq[t] = pr + rem;
+    }
+  }
+  for (int base = i0; base < i1; base += 32) {
+    __syncthreads();
+    for (int x = tid; x < 32 * kWY; x += kWyThreads) {
+      const int rr = x / kWY, pr = x % kWY, i = base + rr;
+      ys[rr * kWY + pr] = (i < i1 && pr < nr) ? u[(size_t)(j0 + pr) * m + i] : dw::make(0.f);
+    }
+    __syncthreads();
+    const int nrr = min(32, i1 - base);
+    for (int rr = 0; rr < nrr; ++rr)
+#pragma unroll
+      for (int t = 0; t < kPer; ++t)
+        if (pp[t] >= 0) acc[t] = dw::add(acc[t], dw::mul(ys[rr * kWY + pp[t]], ys[rr * kWY + qq[t]]));
+  }
+  df* gp = gpart + ((size_t)b * S + part) * kWY * kWY;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t)
+    if (pp[t] >= 0) gp[pp[t] * kWY + qq[t]] = acc[t];
+}
+
+// T_b by the forward recurrence T[0:i, i] = -tau_i T[0:i, 0:i] (Y^T y_i),
+// T[i, i] = tau_i.  One warp per block.
+__global__ void __launch_bounds__(32) wy_t_kernel(const df* __restrict__ gpart, const df* __restrict__ tau,
+                                                  int nrefl, int S, df* __restrict__ tblk) {
+  __shared__ df gs[kWY * kWY];
+  __shared__ df ts[kWY * kWY];
+  __shared__ df tmp[kWY];
+  const int b = blockIdx.x, lane = threadIdx.x;
+  const int j0 = b * kWY, nr = min(kWY, nrefl - j0);
+  for (int x = lane; x < kWY * kWY; x += 32) {
+    const int pr = x / kWY, q = x % kWY;
+    df v = dw::make(0.f);
+    if (pr <= q)
+      for (int part = 0; part < S; ++part) v = dw::add(v, gpart[((size_t)b * S + part) * kWY * kWY + x]);
+    gs[x] = v;
+    ts[x] = dw::make(0.f);
+  }
+  __syncwarp();
+  for (int i = 0; i < nr; ++i) {
+    const df ti = tau[j0 + i];
+    if (lane < i) tmp[lane] = dw::neg(dw::mul(ti, gs[lane * kWY + i]));
+    __syncwarp();
+    df v = dw::make(0.f);
+    if (lane < i)
+      for (int q = lane; q < i; ++q) v = dw::add(v, dw::mul(ts[lane * kWY + q], tmp[q]));
+    __syncwarp();
+    if (lane < i) ts[lane * kWY + i] = v;
+    if (lane == 0) ts[i * kWY + i] = ti;
+    __syncwarp();
+  }
+  for (int x = lane; x < kWY * kWY; x += 32) tblk[(size_t)b * kWY * kWY + x] = ts[x];
+}
+
+// Two columns of Z per CTA: z <- B_b z for b = nbk-1 .. 0, with
+// B_b z = z - Y_b (T_b (Y_b^T z)); writes V[:, c] in fp64.  Each thread
+// carries four independent double-word accumulations (two reflectors or
+// two rows, times two columns) to hide their dependent latency.
+constexpr int kApThreads = 512;
+__global__ void __launch_bounds__(kApThreads) wy_apply_kernel(const df* __restrict__ u, const df* __restrict__ tblk,
+                                                              int m, int nrefl, int k, const df* __restrict__ z,
+                                                              double* __restrict__ v) {
   extern __shared__ df smd[];
-  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
-  const int m = a.m, k = a.k;
-  unsigned target = 0;
-  // phase 0: partial Gram matrices Y_b^T Y_b over row slices
-  if (cta < a.nbk * a.S) {
-    df* ys = smd;  // [32 rows][kWY]
-    const int b = cta / a.S, part = cta % a.S;
-    const int j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
-    const int rbeg = j0 + 1, rows = m - rbeg;
-    const int per = (rows + a.S - 1) / a.S;
-    const int i0 = rbeg + part * per, i1 = min(m, i0 + per);
-    df acc0 = dw::make(0.f), acc1 = dw::make(0.f);
-    const int np = kWY * (kWY + 1) / 2;
-    int p0 = -1, q0 = -1, p1 = -1, q1 = -1;
-    for (int idx = tid, t = 0; idx < np && t < 2; idx += kBtThreads, ++t) {
-      int p = 0, rem = idx;
-      while (rem >= kWY - p) { rem -= kWY - p; ++p; }
-      if (t == 0) { p0 = p; q0 = p + rem; } else { p1 = p; q1 = p + rem; }
-    }
-    for (int base = i0; base < i1; base += 32) {
-      __syncthreads();
-      for (int x = tid; x < 32 * kWY; x += kBtThreads) {
-        const int rr = x / kWY, p = x % kWY, i = base + rr;
-        ys[rr * kWY + p] = (i < i1 && p < nr) ? a.u[(size_t)(j0 + p) * m + i] : dw::make(0.f);
-      }
-      __syncthreads();
-      const int nrr = min(32, i1 - base);
-      for (int rr = 0; rr < nrr; ++rr) {
-        if (p0 >= 0) acc0 = dw::add(acc0, dw::mul(ys[rr * kWY + p0], ys[rr * kWY + q0]));
-        if (p1 >= 0) acc1 = dw::add(acc1, dw::mul(ys[rr * kWY + p1], ys[rr * kWY + q1]));
-      }
-    }
-    df* gp = a.gpart + ((size_t)b * a.S + part) * kWY * kWY;
-    if (p0 >= 0) gp[p0 * kWY + q0] = acc0;
-    if (p1 >= 0) gp[p1 * kWY + q1] = acc1;
+  df* z0 = smd;               // [m]
+  df* z1 = z0 + m;            // [m]
+  df* ts = z1 + m;            // [32 x 32]
+  df* wv = ts + kWY * kWY;    // [2][32]
+  df* tv = wv + 2 * kWY;      // [2][32]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kApThreads / 32;
+  const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
+  const bool has1 = c1 < k;
+  for (int i = tid; i < m; i += kApThreads) {
+    z0[i] = z[(size_t)i * k + c0];
+    z1[i] = has1 ? z[(size_t)i * k + c1] : dw::make(0.f);
   }
-  if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
-  // phase 1: T_b by the forward recurrence T[0:i, i] = -tau_i T[0:i, 0:i] (Y^T y_i)
-  if (cta < a.nbk) {
-    df* gs = smd;                 // [32][32]
-    df* ts = gs + kWY * kWY;      // [32][32]
-    df* tmp = ts + kWY * kWY;     // [32]
-    const int b = cta, j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
-    for (int x = tid; x < kWY * kWY; x += kBtThreads) {
-      const int p = x / kWY, q = x % kWY;
-      df s = dw::make(0.f);
-      if (p <= q)
-        for (int part = 0; part < a.S; ++part) s = dw::add(s, a.gpart[((size_t)b * a.S + part) * kWY * kWY + x]);
-      gs[x] = s;
-      ts[x] = dw::make(0.f);
-    }
-    __syncthreads();
-    for (int i = 0; i < nr; ++i) {
-      const df ti = a.tau[j0 + i];
-      if (tid < i) tmp[tid] = dw::neg(dw::mul(ti, gs[tid * kWY + i]));
-      __syncthreads();
-      df s = dw::make(0.f);
-      if (tid < i)
-        for (int q = tid; q < i; ++q) s = dw::add(s, dw::mul(ts[tid * kWY + q], tmp[q]));
-      __syncthreads();
-      if (tid < i) ts[tid * kWY + i] = s;
-      if (tid == 0) ts[i * kWY + i] = ti;
-      __syncthreads();
-    }
-    for (int x = tid; x < kWY * kWY; x += kBtThreads) a.tblk[(size_t)b * kWY * kWY + x] = ts[x];
-  }
-  if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
-  // phase 2: blocks from last to first on a fixed row partition
-  const int per = (m + G - 1) / G;
-  const int r0 = cta * per, r1 = min(m, r0 + per);
-  df* ys = smd;                        // [per][kWY]
-  df* zs = ys + (size_t)per * kWY;     // [per][k]
-  df* wsm = zs + (size_t)per * k;      // [kWY][k]
-  df* wc = wsm + (size_t)kWY * k;      // [kWY]
-  df* wsl = wc + kWY;                  // [kBtThreads]
-  for (int x = tid; x < max(0, r1 - r0) * k; x += kBtThreads) zs[x] = a.z[(size_t)r0 * k + x];
-  for (int b = a.nbk - 1; b >= 0; --b) {
-    const int j0 = b * kWY, nr = min(kWY, a.nrefl - j0);
-    const int lo = max(r0, j0 + 1);
-    const int nrow = max(0, r1 - lo);
-    const int off = lo - r0;  // first local row
-    // (a) Y^T Z over my rows
-    for (int x = tid; x < nrow * kWY; x += kBtThreads) {
-      const int rr = x / kWY, p = x % kWY;
-      ys[x] = p < nr ? a.u[(size_t)(j0 + p) * m + lo + rr] : dw::make(0.f);
-    }
-    __syncthreads();
-    df* wp = a.wpart + (size_t)cta * kWY * k;
-    for (int x = tid; x < kWY * k; x += kBtThreads) {
-      const int p = x / k, c = x % k;
-      df s = dw::make(0.f);
-      for (int rr = 0; rr < nrow; ++rr) s = dw::add(s, dw::mul(ys[rr * kWY + p], zs[(off + rr) * k + c]));
-      wp[x] = s;
-    }
-    if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
-    // (b) column c of W = sum over CTAs, then T_b W
-    for (int c = cta; c < k; c += G) {
-      {
-        const int p = tid % kWY, sl = tid / kWY, nsl = kBtThreads / kWY;
-        df s = dw::make(0.f);
-        for (int g2 = sl; g2 < G; g2 += nsl) {
-          const float2 t = __ldcg(reinterpret_cast<const float2*>(a.wpart + (size_t)g2 * kWY * k + p * k + c));
-          s = dw::add(s, dw::make(t.x, t.y));
+  const int nbk = (nrefl + kWY - 1) / kWY;
+  for (int b = nbk - 1; b >= 0; --b) {
+    const int j0 = b * kWY, nr = min(kWY, nrefl - j0);
+    for (int x = tid; x < kWY * kWY; x += kApThreads) ts[x] = tblk[(size_t)b * kWY * kWY + x];
+    // w = Y^T z over rows >= j0 + 1: warp takes reflectors warp and warp + 16
+    {
+      const int pa = warp, pb = warp + kWarps;
+      const df* ya = u + (size_t)(j0 + pa) * m;
+      const df* yb = u + (size_t)(j0 + pb) * m;
+      const bool va = pa < nr, vb = pb < nr;
+      df a0 = dw::make(0.f), a1 = a0, b0 = a0, b1 = a0;
+      // four rows per lane per iteration, their loads issued together
+      for (int i = j0 + 1 + lane; i < m; i += 128) {
+        df ra[4], rb[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int ii = i + 32 * t;
+          const bool in = ii < m;
+          ra[t] = (va && in) ? ya[ii] : dw::make(0.f);
+          rb[t] = (vb && in) ? yb[ii] : dw::make(0.f);
         }
-        wsl[sl * kWY + p] = s;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int ii = i + 32 * t;
+          if (ii < m) {
+            const df zi0 = z0[ii], zi1 = z1[ii];
+            a0 = dw::add(a0, dw::mul(ra[t], zi0));
+            a1 = dw::add(a1, dw::mul(ra[t], zi1));
+            b0 = dw::add(b0, dw::mul(rb[t], zi0));
+            b1 = dw::add(b1, dw::mul(rb[t], zi1));
+          }
+        }
       }
-      __syncthreads();
-      if (tid < kWY) {
-        df s = dw::make(0.f);
-        for (int sl = 0; sl < kBtThreads / kWY; ++sl) s = dw::add(s, wsl[sl * kWY + tid]);
-        wc[tid] = s;
+      a0 = dw::warp_sum(a0);
+      a1 = dw::warp_sum(a1);
+      b0 = dw::warp_sum(b0);
+      b1 = dw::warp_sum(b1);
+      if (lane == 0) {
+        if (va) { wv[pa] = a0; wv[kWY + pa] = a1; }
+        if (vb) { wv[pb] = b0; wv[kWY + pb] = b1; }
       }
-      __syncthreads();
-      if (tid < kWY) {
-        const df* tb = a.tblk + (size_t)b * kWY * kWY;
-        df s = dw::make(0.f);
-        for (int q = tid; q < kWY; ++q) s = dw::add(s, dw::mul(tb[tid * kWY + q], wc[q]));
-        a.wfull[tid * k + c] = s;
-      }
-      __syncthreads();
-    }
-    if (!grid_sync(a.bar, G, target, a.abort_flag, a.status)) return;
-    // (c) Z -= Y (T W) on my rows
-    for (int x = tid; x < kWY * k; x += kBtThreads) {
-      const float2 t = __ldcg(reinterpret_cast<const float2*>(a.wfull + x));
-      wsm[x] = dw::make(t.x, t.y);
     }
     __syncthreads();
-    for (int x = tid; x < nrow * k; x += kBtThreads) {
-      const int rr = x / k, c = x % k;
-      df s = zs[(off + rr) * k + c];
-      for (int p = 0; p < kWY; ++p) s = dw::sub(s, dw::mul(ys[rr * kWY + p], wsm[p * k + c]));
-      zs[(off + rr) * k + c] = s;
+    // t = T w (upper triangular), both columns
+    if (warp < 2) {
+      df acc = dw::make(0.f);
+      if (lane < nr)
+        for (int q = lane; q < nr; ++q) acc = dw::add(acc, dw::mul(ts[lane * kWY + q], wv[warp * kWY + q]));
+      tv[warp * kWY + lane] = acc;
+    }
+    __syncthreads();
+    // z -= Y t: thread takes rows i and i + kApThreads
+    for (int i = j0 + 1 + tid; i < m; i += 2 * kApThreads) {
+      const int i2 = i + kApThreads;
+      const bool v2 = i2 < m;
+      df s0 = dw::make(0.f), s1 = s0, r0 = s0, r1 = s0;
+      // eight reflectors per iteration, their loads issued together
+      for (int p0 = 0; p0 < nr; p0 += 8) {
+        df ya[8], yb[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int pr = p0 + t;
+          const df* y = u + (size_t)(j0 + pr) * m;
+          ya[t] = pr < nr ? y[i] : dw::make(0.f);
+          yb[t] = (pr < nr && v2) ? y[i2] : dw::make(0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int pr = p0 + t;
+          if (pr < nr) {
+            const df t0 = tv[pr], t1 = tv[kWY + pr];
+            s0 = dw::add(s0, dw::mul(ya[t], t0));
+            s1 = dw::add(s1, dw::mul(ya[t], t1));
+            r0 = dw::add(r0, dw::mul(yb[t], t0));
+            r1 = dw::add(r1, dw::mul(yb[t], t1));
+          }
+        }
+      }
+      z0[i] = dw::sub(z0[i], s0);
+      z1[i] = dw::sub(z1[i], s1);
+      if (v2) {
+        z0[i2] = dw::sub(z0[i2], r0);
+        z1[i2] = dw::sub(z1[i2], r1);
+      }
     }
     __syncthreads();
   }
-  for (int x = tid; x < max(0, r1 - r0) * k; x += kBtThreads) a.v[(size_t)r0 * k + x] = dw::to_double(zs[x]);
+  for (int i = tid; i < m; i += kApThreads) {
+    v[(size_t)i * k + c0] = dw::to_double(z0[i]);
+    if (has1) v[(size_t)i * k + c1] = dw::to_double(z1[i]);
+  }
 }
 
 // Z (double-word) to fp64, for m <= 2 (no reflectors).
@@ -1032,7 +1216,7 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
     FKK_CUDA(ctx, cudaFuncSetAttribute(tri_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     FKK_COUNT_LAUNCH();
     tri_bisect_kernel<<<k, kBisWarps * 32, sb, st>>>(dd, ee, m, lam_s);
-    const size_t sv = (size_t)5 * m * sizeof(df) + (size_t)m * sizeof(double);
+    const size_t sv = (size_t)6 * m * sizeof(df) + (size_t)m * sizeof(int);
     FKK_CUDA(ctx, cudaFuncSetAttribute(tri_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv));
     FKK_COUNT_LAUNCH();
     tri_vec_kernel<<<k, 32, sv, st>>>(dd, ee, m, k, lam_s, z, ctx->d_status);
@@ -1044,29 +1228,20 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   const int nrefl = std::max(0, m - 2);
   if (nrefl > 0) {
     const int nbk = (nrefl + kWY - 1) / kWY;
-    const int G = nsm;
-    const int S = std::max(1, G / nbk);
-    const int per = (m + G - 1) / G;
+    const int S = std::max(1, std::min(8, nsm / nbk));
     df* gpart = (df*)workspace(ctx, "tri_gpart", (size_t)nbk * S * kWY * kWY * sizeof(df), &s);
     if (!gpart) return s;
     df* tblk = (df*)workspace(ctx, "tri_tblk", (size_t)nbk * kWY * kWY * sizeof(df), &s);
     if (!tblk) return s;
-    df* wpart = (df*)workspace(ctx, "tri_wpart", (size_t)G * kWY * k * sizeof(df), &s);
-    if (!wpart) return s;
-    df* wfull = (df*)workspace(ctx, "tri_wfull", (size_t)kWY * k * sizeof(df), &s);
-    if (!wfull) return s;
-    const size_t sbt = std::max<size_t>((size_t)(3 * kWY * kWY + kWY),
-                                        (size_t)per * (kWY + k) + (size_t)kWY * k + kWY + kBtThreads) *
-                       sizeof(df);
-    BackArgs ba{u, tau, m, nrefl, k, nbk, S, z, vz, gpart, tblk, wpart, wfull, scr + 32, (int*)(scr + 36),
-                ctx->d_status};
-    void* args[] = {&ba};
-    FKK_CUDA(ctx, cudaFuncSetAttribute(back_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbt));
-    int per_sm = 0;
-    FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, back_wy_kernel, kBtThreads, sbt));
-    if (per_sm < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: back-transformation cannot be resident");
     FKK_COUNT_LAUNCH();
-    FKK_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)back_wy_kernel, dim3(G), dim3(kBtThreads), args, sbt, st));
+    wy_gram_kernel<<<dim3(nbk, S), kWyThreads, 0, st>>>(u, m, nrefl, S, gpart);
+    FKK_COUNT_LAUNCH();
+    wy_t_kernel<<<nbk, 32, 0, st>>>(gpart, tau, nrefl, S, tblk);
+    const size_t sa = ((size_t)2 * m + kWY * kWY + 4 * kWY) * sizeof(df);
+    FKK_CUDA(ctx, cudaFuncSetAttribute(wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    FKK_COUNT_LAUNCH();
+    wy_apply_kernel<<<(k + 1) / 2, kApThreads, sa, st>>>(u, tblk, m, nrefl, k, z, vz);
+    FKK_CUDA(ctx, cudaGetLastError());
   } else {
     FKK_COUNT_LAUNCH();
     df_to_double_kernel<<<(m * k + 255) / 256, 256, 0, st>>>(z, m * k, vz);
