@@ -7,6 +7,7 @@
 //   H_Phi = H{Phi_PEC^T};  V_SEC^T = M{B + H_Phi}              (Eq. fSEC_VT)
 //   C_amp = B + H_Phi - V_SEC^T;  C_ph = H_B - Phi_PEC^T       (Eq. fKKEC)
 #include "common.cuh"
+#include "df64.cuh"
 #include "fft.cuh"
 #include "fit.h"
 
@@ -16,28 +17,37 @@ namespace {
 // ------------------------------------------------------------------ q ---
 __global__ void gather_q_kernel(const int64_t* __restrict__ qmax, const int64_t* __restrict__ qmin, int k,
                                 int64_t n_rows, int64_t* __restrict__ q, int* __restrict__ nq, long long* status) {
-  if (threadIdx.x != 0) return;
-  int64_t buf[160];
-  int n = 0;
-  for (int i = 0; i < k; ++i) { buf[n++] = qmax[i]; buf[n++] = qmin[i]; }
-  // a column of P without a finite value has no extreme row: report it and
-  // use row 0 rather than index past P
-  for (int a = 0; a < n; ++a)
-    if (buf[a] < 0 || buf[a] >= n_rows) {
+  // the 2k extreme rows, sorted by rank (position = number of smaller values,
+  // ties by index), then de-duplicated; one block
+  __shared__ int64_t buf[160], srt[160];
+  __shared__ int keep[160];
+  const int n = 2 * k, t = threadIdx.x;
+  if (t < n) {
+    int64_t v = (t & 1) ? qmin[t >> 1] : qmax[t >> 1];
+    // a column of P without a finite value has no extreme row: report it and
+    // use row 0 rather than index past P
+    if (v < 0 || v >= n_rows) {
       record_error(status, kErrNotConverged);
-      buf[a] = 0;
+      v = 0;
     }
-  for (int a = 1; a < n; ++a) {  // insertion sort
-    int64_t v = buf[a];
-    int b = a - 1;
-    while (b >= 0 && buf[b] > v) { buf[b + 1] = buf[b]; --b; }
-    buf[b + 1] = v;
+    buf[t] = v;
   }
-  int u = 0;
-  for (int a = 0; a < n; ++a)
-    if (u == 0 || buf[a] != buf[u - 1]) buf[u++] = buf[a];
-  for (int a = 0; a < u; ++a) q[a] = buf[a];
-  *nq = u;
+  __syncthreads();
+  if (t < n) {
+    const int64_t v = buf[t];
+    int rank = 0;
+    for (int u = 0; u < n; ++u) rank += (buf[u] < v) || (buf[u] == v && u < t);
+    srt[rank] = v;
+  }
+  __syncthreads();
+  if (t < n) keep[t] = (t == 0 || srt[t] != srt[t - 1]);
+  __syncthreads();
+  if (t == 0) {
+    int u = 0;
+    for (int a = 0; a < n; ++a)
+      if (keep[a]) q[u++] = srt[a];
+    *nq = u;
+  }
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ p, int k, const int64_t* __restrict__ q,
@@ -241,77 +251,107 @@ __global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_a
       z[2 * i + 1] = D[i].y;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] = (y[j] > z[j]) ? p : 1.0 - p;
-    __syncthreads();
+    // new weights; once they repeat, every further iteration reproduces the
+    // same z, so the remaining iterations are skipped
+    int changed = 0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const double nw = (y[j] > z[j]) ? p : 1.0 - p;
+      changed |= nw != w[j];
+      w[j] = nw;
+    }
+    if (!__syncthreads_or(changed)) break;
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) z_all[(int64_t)row * m + j] = z[j];
 }
 
 // -------------------------------------------------------------- ridge ---
-// C = X^T X + lambda_r I with lambda_r = rel * ||X||_F^2 / k; Cholesky in
-// place (lower), one block.  X is nq x k.
-__global__ void ridge_chol_kernel(const double* __restrict__ X, const int* __restrict__ nq_dev, int k, double rel,
-                                  double* __restrict__ Lc) {
-  extern __shared__ double C[];
-  __shared__ double fro;
+// Eq. PEC_Ridge as Phi_PEC^T = N Phi_err with N = (X^T X + lambda_r I)^-1 X^T
+// (k x nq), lambda_r = rel * ||X||_F^2 / k.  ridge_n_kernel forms N in one
+// block in double-word arithmetic (Cholesky with reciprocal pivots, then the
+// two triangular solves on all nq right-hand sides at once); ridge_apply
+// multiplies it out in fp64, one output per thread.
+__global__ void ridge_n_kernel(const double* __restrict__ X, const int* __restrict__ nq_dev, int k, double rel,
+                               double* __restrict__ n_out) {
+  extern __shared__ dw::df rsm[];
   const int nq = *nq_dev;
-  if (threadIdx.x == 0) fro = 0.0;
-  __syncthreads();
-  double part = 0.0;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    int a = t / k, b = t % k;
-    double s = 0.0;
-    for (int r = 0; r < nq; ++r) s = fma(X[(int64_t)r * k + a], X[(int64_t)r * k + b], s);
-    C[t] = s;
-    if (a == b) part += s;
+  dw::df* C = rsm;            // [k][k], lower triangle used
+  dw::df* B = C + k * k;      // [k][nq]: X^T, then the solution
+  dw::df* rinv = B + k * nq;  // [k] reciprocal pivots
+  __shared__ dw::df lam_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int x = tid; x < k * nq; x += nt) {
+    const int i = x / nq, q = x % nq;
+    B[x] = dw::from_double(X[(int64_t)q * k + i]);
   }
-  atomicAdd(&fro, part);
   __syncthreads();
-  const double lam = rel * fro / k;
-  for (int a = threadIdx.x; a < k; a += blockDim.x) C[a * k + a] += lam;
+  for (int x = tid; x < k * k; x += nt) {
+    const int a = x / k, b = x % k;
+    if (b > a) continue;
+    dw::df acc = dw::make(0.f);
+    for (int q = 0; q < nq; ++q) acc = dw::add(acc, dw::mul(B[a * nq + q], B[b * nq + q]));
+    C[x] = acc;
+  }
   __syncthreads();
-  // right-looking Cholesky
+  if (tid == 0) {
+    dw::df tr = dw::make(0.f);
+    for (int a = 0; a < k; ++a) tr = dw::add(tr, C[a * k + a]);
+    lam_s = dw::mul(tr, dw::from_double(rel / k));
+  }
+  __syncthreads();
+  for (int a = tid; a < k; a += nt) C[a * k + a] = dw::add(C[a * k + a], lam_s);
+  __syncthreads();
+  // Cholesky, lower, in place
   for (int c = 0; c < k; ++c) {
-    if (threadIdx.x == 0) C[c * k + c] = sqrt(C[c * k + c]);
+    if (tid == 0) {
+      const dw::df d = dw::sqrt(C[c * k + c]);
+      C[c * k + c] = d;
+      rinv[c] = dw::rcp(d);
+    }
     __syncthreads();
-    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) C[r * k + c] /= C[c * k + c];
+    for (int r = c + 1 + tid; r < k; r += nt) C[r * k + c] = dw::mul(C[r * k + c], rinv[c]);
     __syncthreads();
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-      int r = t / k, s = t % k;
-      if (r > c && s > c && s <= r) C[r * k + s] -= C[r * k + c] * C[s * k + c];
+    const int w = k - c - 1;
+    for (int x = tid; x < w * w; x += nt) {
+      const int r = c + 1 + x / w, t = c + 1 + x % w;
+      if (t <= r) C[r * k + t] = dw::sub(C[r * k + t], dw::mul(C[r * k + c], C[t * k + c]));
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    int r = t / k, s = t % k;
-    Lc[t] = (s <= r) ? C[t] : 0.0;
+  // L Y = X^T
+  for (int i = 0; i < k; ++i) {
+    for (int q = tid; q < nq; q += nt) B[i * nq + q] = dw::mul(B[i * nq + q], rinv[i]);
+    __syncthreads();
+    const int w = k - i - 1;
+    for (int x = tid; x < w * nq; x += nt) {
+      const int t = i + 1 + x / nq, q = x % nq;
+      B[t * nq + q] = dw::sub(B[t * nq + q], dw::mul(C[t * k + i], B[i * nq + q]));
+    }
+    __syncthreads();
   }
+  // L^T N = Y
+  for (int i = k - 1; i >= 0; --i) {
+    for (int q = tid; q < nq; q += nt) B[i * nq + q] = dw::mul(B[i * nq + q], rinv[i]);
+    __syncthreads();
+    for (int x = tid; x < i * nq; x += nt) {
+      const int t = x / nq, q = x % nq;
+      B[t * nq + q] = dw::sub(B[t * nq + q], dw::mul(C[i * k + t], B[i * nq + q]));
+    }
+    __syncthreads();
+  }
+  for (int x = tid; x < k * nq; x += nt) n_out[x] = dw::to_double(B[x]);
 }
 
-// R = X^T Phi_err (k x m), then solve (L L^T) out = R column by column.
-__global__ void ridge_solve_kernel(const double* __restrict__ X, const double* __restrict__ perr,
-                                   const int* __restrict__ nq_dev, int k, int m, const double* __restrict__ Lc,
-                                   double* __restrict__ out) {
+// Phi_PEC^T[i, j] = sum_q N[i, q] Phi_err[q, j].
+__global__ void ridge_apply_kernel(const double* __restrict__ nmat, const double* __restrict__ perr,
+                                   const int* __restrict__ nq_dev, int k, int m, double* __restrict__ out) {
+  const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const int nq = *nq_dev;
-  double r[80];
-  for (int i = 0; i < k; ++i) r[i] = 0.0;
-  for (int q = 0; q < nq; ++q) {
-    double e = perr[(int64_t)q * m + j];
-    for (int i = 0; i < k; ++i) r[i] = fma(X[(int64_t)q * k + i], e, r[i]);
-  }
-  for (int i = 0; i < k; ++i) {  // L y = r
-    double s = r[i];
-    for (int t = 0; t < i; ++t) s -= Lc[i * k + t] * r[t];
-    r[i] = s / Lc[i * k + i];
-  }
-  for (int i = k - 1; i >= 0; --i) {  // L^T x = y
-    double s = r[i];
-    for (int t = i + 1; t < k; ++t) s -= Lc[t * k + i] * r[t];
-    r[i] = s / Lc[i * k + i];
-  }
-  for (int i = 0; i < k; ++i) out[(int64_t)i * m + j] = r[i];
+  const double* nr = nmat + (int64_t)i * nq;
+  double acc = 0.0;
+  for (int q = 0; q < nq; ++q) acc = fma(nr[q], perr[(int64_t)q * m + j], acc);
+  out[(int64_t)i * m + j] = acc;
 }
 
 // ---------------------------------------------------------------- SEC ---
@@ -453,7 +493,7 @@ __global__ void axpy3_kernel(const double* __restrict__ a, const double* __restr
 
 fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
                            int64_t n_rows, int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st) {
-  FKK_COUNT_LAUNCH(); gather_q_kernel<<<1, 32, 0, st>>>(qmax, qmin, k, n_rows, q, nq_dev, ctx->d_status);
+  FKK_COUNT_LAUNCH(); gather_q_kernel<<<1, 160, 0, st>>>(qmax, qmin, k, n_rows, q, nq_dev, ctx->d_status);
   FKK_COUNT_LAUNCH(); gather_rows_kernel<<<2 * k, 32, 0, st>>>(p, k, q, nq_dev, x_rows);
   return cuda_check(ctx, cudaGetLastError(), "gather_q launch");
 }
@@ -494,7 +534,7 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
     if (!phph) return s;
     double* perr = (double*)workspace(ctx, "bm_perr", (size_t)nq_max * m * 8, &s);
     if (!perr) return s;
-    double* lc = (double*)workspace(ctx, "bm_chol", (size_t)k * k * 8, &s);
+    double* lc = (double*)workspace(ctx, "bm_ridge_n", (size_t)k * nq_max * 8, &s);
     if (!lc) return s;
     FKK_COUNT_LAUNCH(); small_gemm_kernel<<<dim3(nq_max, 4), 256, k * sizeof(double), st>>>(x_rows, hb, k, m, phph, nq_dev);
     int P = 1;
@@ -502,8 +542,10 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
     size_t als_smem = (size_t)P * (3 * sizeof(Blk) + sizeof(double2)) + (size_t)6 * P * sizeof(double);
     FKK_CUDA(ctx, cudaFuncSetAttribute(als_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)als_smem));
     FKK_COUNT_LAUNCH(); als_kernel<<<nq_max, 256, als_smem, st>>>(phph, m, P, bp.als_lambda, bp.als_p, bp.als_iters, perr, nq_dev);
-    FKK_COUNT_LAUNCH(); ridge_chol_kernel<<<1, 256, (size_t)k * k * sizeof(double), st>>>(x_rows, nq_dev, k, bp.ridge_rel, lc);
-    FKK_COUNT_LAUNCH(); ridge_solve_kernel<<<(m + 63) / 64, 64, 0, st>>>(x_rows, perr, nq_dev, k, m, lc, phit);
+    const size_t rsm = (size_t)(k * k + k * nq_max + k) * sizeof(dw::df);
+    FKK_CUDA(ctx, cudaFuncSetAttribute(ridge_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    FKK_COUNT_LAUNCH(); ridge_n_kernel<<<1, 256, rsm, st>>>(x_rows, nq_dev, k, bp.ridge_rel, lc);
+    FKK_COUNT_LAUNCH(); ridge_apply_kernel<<<dim3((m + 127) / 128, k), 128, 0, st>>>(lc, perr, nq_dev, k, m, phit);
     FKK_CUDA(ctx, cudaGetLastError());
     FKK_TRY(hilbert_rows(ctx, phit, k, m, L, hphi, nullptr, st));
   } else {
