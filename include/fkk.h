@@ -263,6 +263,74 @@ fkk_status fkk_reconstruct(fkk_ctx* ctx, const float* p, int64_t n_spectra, int3
                            const double* c_amp, const double* c_ph, float* im_out, float* re_out, int64_t ld_out,
                            void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Trained-basis files, the noise model, and serving (Sec. 2.6)         */
+/* ------------------------------------------------------------------ */
+
+/* Write the basis (all trained arrays: f, S, V, W, B, H_B, Phi_PEC, H_Phi,
+ * V_SEC, C_amp, C_ph, q, I_ref, and the fit parameters) to a file: a
+ * header with format version, sizes and an FNV-1a checksum of the data.
+ * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_CUDA, FKK_ERR_BAD_FILE (cannot
+ * write). */
+fkk_status fkk_basis_save(const fkk_basis* basis, const char* path);
+
+/* Read a file written by fkk_basis_save into a new basis on ctx's device
+ * (owned by the caller, release with fkk_basis_free).  A file with another
+ * magic, version or parameter layout, inconsistent sizes, truncated data or
+ * a wrong checksum gives FKK_ERR_BAD_FILE and no basis. */
+fkk_status fkk_basis_load(fkk_ctx* ctx, const char* path, fkk_basis** out);
+
+/* f(w) of the noise model (Sec. 2.2): f = 2 <I> / sqrt(alpha <I> +
+ * sigma_g^2) per channel, from the mean spectrum <I> (device floats,
+ * n_channels) into f_out (device doubles); pass f to fkk_fit_basis as the
+ * f_or_null weights (after conversion to float) when fitting with a
+ * precomputed noise model.  alpha, sigma_g >= 0, not both 0. */
+fkk_status fkk_noise_scale(fkk_ctx* ctx, const float* mean_spectrum, int32_t n_channels, double alpha,
+                           double sigma_g, double* f_out, void* stream);
+
+/* Serving of a trained basis (Sec. 2.6, Eq. ML_Unew then Eq. fKKEC).  A
+ * server runs one worker thread with its own stream and its own context on
+ * the basis' device (same HBM budget as ctx, workspace separate from ctx's).
+ * Submitted tiles queue in order; the worker gathers consecutive tiles into
+ * one batch up to its staging size (continuous batching), runs the apply
+ * once and scatters the results.  Larger tiles run alone (device tiles in
+ * place, host tiles in staging-sized chunks).  The basis must outlive the
+ * server. */
+typedef struct fkk_server fkk_server;
+typedef uint64_t fkk_req;
+
+/* tune_cache_or_null: a text file holding "max_batch=<spectra>"; when the
+ * path is given but holds no entry, a short calibration of the apply at
+ * batch sizes 2048, 4096, ... picks the smallest within 10% of the best
+ * throughput and writes it there.  Without a path the staging size is the
+ * largest power of two <= 65,536 spectra that fits the budget. */
+fkk_status fkk_serve_start(fkk_ctx* ctx, const fkk_basis* basis, const char* tune_cache_or_null, fkk_server** out);
+
+/* Queue a tile of n_spectra spectra (n_channels of the basis each, rows
+ * contiguous) and return its id at once.  tile_on_host = 0: tile and
+ * im_out are device pointers; 1: both are pinned host memory.  The buffers
+ * belong to the caller and must stay valid until the request is waited.
+ * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_SHUTDOWN (server stopping). */
+fkk_status fkk_serve_submit(fkk_server* server, const float* tile, int64_t n_spectra, int32_t tile_on_host,
+                            float* im_out, fkk_req* out_id);
+
+/* Wait for a request: its status (FKK_OK, a CUDA error, or
+ * FKK_ERR_SHUTDOWN if the server stopped before it ran), after which the id
+ * is released; FKK_ERR_TIMEOUT if it has not completed within timeout_ms
+ * (< 0: no limit), the id stays valid; FKK_ERR_INVALID_ARG for an unknown
+ * or already released id.  Each request is waited by one thread. */
+fkk_status fkk_serve_wait(fkk_server* server, fkk_req id, int32_t timeout_ms);
+
+/* p50 / p99 of submit-to-completion latency over the last 16,384 requests
+ * and the throughput (spectra completed per second since the first
+ * submit).  Any pointer may be NULL. */
+fkk_status fkk_serve_stats(fkk_server* server, double* p50_ms, double* p99_ms, double* spectra_per_s);
+
+/* Stop: queued requests complete with FKK_ERR_SHUTDOWN, a batch already
+ * running finishes, threads blocked in fkk_serve_wait return, and the
+ * server (its stream, context and staging) is freed. */
+fkk_status fkk_serve_stop(fkk_server* server);
+
 /* Largest problem fkk_reconstruct_noalloc accepts in one call. */
 #define FKK_NOALLOC_MAX_SPECTRA 16384
 #define FKK_NOALLOC_MAX_CHANNELS 2048

@@ -17,20 +17,23 @@ from ._lib import (  # noqa: F401
     fit_params,
     fkk_apply,
     fkk_basis_from_arrays,
+    fkk_basis_load,
     fkk_basis_math,
     fkk_eig_topk,
     fkk_fit_basis,
     fkk_gram,
+    fkk_noise_scale,
     fkk_project,
     fkk_reconstruct,
     fkk_reconstruct_noalloc,
     kk_per_spectrum,
     launch_count,
     lib,
+    Server,
 )
 
 __all__ = [
     "Basis", "Context", "FitParams", "FkkError", "SEC_MEAN", "SEC_SAVGOL", "fit_params", "fkk_apply",
-    "fkk_basis_from_arrays", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_gram", "fkk_project",
+    "fkk_basis_from_arrays", "fkk_basis_load", "fkk_noise_scale", "Server", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_gram", "fkk_project",
     "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "launch_count", "lib",
 ]

@@ -66,6 +66,14 @@ SIGNATURES = {
     "fkk_basis_math": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_reconstruct": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
     "fkk_reconstruct_noalloc": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
+    "fkk_basis_save": (_I32, [_P, C.c_char_p]),
+    "fkk_basis_load": (_I32, [_P, C.c_char_p, C.POINTER(_P)]),
+    "fkk_noise_scale": (_I32, [_P, _P, _I32, _F64, _F64, _P, _P]),
+    "fkk_serve_start": (_I32, [_P, _P, C.c_char_p, C.POINTER(_P)]),
+    "fkk_serve_submit": (_I32, [_P, _P, _I64, _I32, _P, C.POINTER(C.c_uint64)]),
+    "fkk_serve_wait": (_I32, [_P, C.c_uint64, _I32]),
+    "fkk_serve_stats": (_I32, [_P, C.POINTER(_F64), C.POINTER(_F64), C.POINTER(_F64)]),
+    "fkk_serve_stop": (_I32, [_P]),
 }
 
 
@@ -260,6 +268,12 @@ class Basis:
             raise FkkError(st, f"fkk_basis_get({which})")
         return out
 
+    def save(self, path: str):
+        """Write the basis to a file (fkk_basis_save)."""
+        st = lib().fkk_basis_save(self._h, str(path).encode())
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_basis_save")
+
     def close(self):
         if self._h:
             lib().fkk_basis_free(self._h)
@@ -406,3 +420,79 @@ def fkk_reconstruct_noalloc(ctx: Context, p, c_amp, c_ph, im_out, re_out=None, s
                                        _ptr(re_out), im_out.stride(0), _stream(stream))
     ctx.check(st, "fkk_reconstruct_noalloc")
     return (im_out, re_out) if re_out is not None else im_out
+
+
+def fkk_basis_load(ctx: Context, path: str) -> Basis:
+    """Read a basis file written by Basis.save onto ctx's device."""
+    h = _P()
+    st = lib().fkk_basis_load(ctx.handle, str(path).encode(), C.byref(h))
+    ctx.check(st, "fkk_basis_load")
+    return Basis(h, ctx)
+
+
+def fkk_noise_scale(ctx: Context, mean_spectrum, alpha: float, sigma_g: float, stream=None):
+    """f = 2 <I> / sqrt(alpha <I> + sigma_g^2) (fp64 device tensor) from a
+    device float tensor of the mean spectrum."""
+    import torch
+
+    _dense(mean_spectrum, "mean_spectrum")
+    m = mean_spectrum.shape[0]
+    f = torch.empty(m, dtype=torch.float64, device=mean_spectrum.device)
+    st = lib().fkk_noise_scale(ctx.handle, _ptr(mean_spectrum), m, alpha, sigma_g, _ptr(f), _stream(stream))
+    ctx.check(st, "fkk_noise_scale")
+    return f
+
+
+class Server:
+    """Serving of a trained basis (fkk_serve_*): submit tiles, wait by id.
+
+    Tiles and outputs are caller-owned: device tensors, or pinned host
+    tensors (``tile.is_pinned()``), and must stay alive until waited."""
+
+    def __init__(self, ctx: Context, basis: Basis, tune_cache=None):
+        self._h = _P()
+        self.ctx = ctx
+        self.basis = basis
+        self._keep = {}
+        st = lib().fkk_serve_start(ctx.handle, basis.handle, str(tune_cache).encode() if tune_cache else None,
+                                   C.byref(self._h))
+        ctx.check(st, "fkk_serve_start")
+
+    def submit(self, tile, im_out) -> int:
+        host = 0 if tile.is_cuda else 1
+        if host and not (tile.is_pinned() and im_out.is_pinned()):
+            raise ValueError("host tiles and outputs must be pinned")
+        if tile.is_cuda != im_out.is_cuda:
+            raise ValueError("tile and output must both be on the device or both on the host")
+        _dense(tile, "tile")
+        _dense(im_out, "im_out")
+        rid = C.c_uint64()
+        st = lib().fkk_serve_submit(self._h, _ptr(tile), tile.shape[0], host, _ptr(im_out), C.byref(rid))
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_serve_submit")
+        self._keep[rid.value] = (tile, im_out)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> int:
+        """Status of the request (0 = done); FKK_ERR_TIMEOUT leaves it pending."""
+        st = lib().fkk_serve_wait(self._h, rid, timeout_ms)
+        if st != -4:
+            self._keep.pop(rid, None)
+        return st
+
+    def stats(self):
+        p50, p99, rate = _F64(), _F64(), _F64()
+        lib().fkk_serve_stats(self._h, C.byref(p50), C.byref(p99), C.byref(rate))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "spectra_per_s": rate.value}
+
+    def stop(self):
+        if self._h:
+            lib().fkk_serve_stop(self._h)
+            self._h = _P()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -1,6 +1,7 @@
 // C-ABI entry points of the fKK-EC fit, the ML apply, the basis object and
 // the individual pipeline steps (include/fkk.h).
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -95,6 +96,14 @@ BasisParams basis_params(const fkk_fit_params& p, int m, int L) {
   return bp;
 }
 
+// Bytes of the single device block backing a basis of m channels and k
+// vectors (the layout basis_alloc carves up).
+size_t basis_block_bytes(int m, int k) {
+  const size_t mk = (size_t)m * k;
+  const size_t doubles = (size_t)m + 2 * k + 2 * mk + 7 * mk;
+  return doubles * 8 + (size_t)2 * k * 8 + 64 + (size_t)m * 4 + 256;
+}
+
 fkk_basis* basis_alloc(fkk_ctx* ctx, int m, int k, fkk_status* st) {
   fkk_basis* b = new (std::nothrow) fkk_basis();
   if (!b) {
@@ -102,9 +111,7 @@ fkk_basis* basis_alloc(fkk_ctx* ctx, int m, int k, fkk_status* st) {
     return nullptr;
   }
   const size_t mk = (size_t)m * k;
-  size_t doubles = (size_t)m + 2 * k + 2 * mk + 7 * mk;
-  size_t bytes = doubles * 8 + (size_t)2 * k * 8 + 64 + (size_t)m * 4 + 256;
-  cudaError_t e = cudaMalloc(&b->block, bytes);
+  cudaError_t e = cudaMalloc(&b->block, basis_block_bytes(m, k));
   if (e != cudaSuccess) {
     *st = cuda_check(ctx, e, "cudaMalloc(basis)");
     delete b;
@@ -300,6 +307,96 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
     return s;
   }
   B->params.pec = 0;  // no sub-sample to report
+  *out = B;
+  return FKK_OK;
+}
+
+// ------------------------------------------------------ save / load ---
+// File: 8-byte magic, u32 format version, u32 sizeof(fkk_fit_params),
+// i32 m, k, pad_len, u32 0, u64 block bytes, u64 FNV-1a of the block, the
+// parameter struct, then the device block byte for byte (all arrays of the
+// basis in the layout basis_alloc defines).
+namespace {
+constexpr char kMagic[8] = {'F', 'K', 'K', 'B', 'A', 'S', 'I', 'S'};
+constexpr uint32_t kFormat = 1;
+struct FileHead {
+  char magic[8];
+  uint32_t version;
+  uint32_t params_size;
+  int32_t m, k, L;
+  uint32_t pad;
+  uint64_t block_bytes;
+  uint64_t checksum;
+};
+uint64_t fnv1a(const uint8_t* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+}  // namespace
+
+fkk_status fkk_basis_save(const fkk_basis* b, const char* path) {
+  if (!b || !path) return FKK_ERR_INVALID_ARG;
+  const size_t bytes = basis_block_bytes(b->m, b->k);
+  std::vector<uint8_t> host(bytes);
+  if (cudaSetDevice(b->device) != cudaSuccess) return FKK_ERR_CUDA;
+  if (cudaMemcpy(host.data(), b->block, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return FKK_ERR_CUDA;
+  FileHead h{};
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = kFormat;
+  h.params_size = sizeof(fkk_fit_params);
+  h.m = b->m;
+  h.k = b->k;
+  h.L = b->L;
+  h.block_bytes = bytes;
+  h.checksum = fnv1a(host.data(), bytes);
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return FKK_ERR_BAD_FILE;
+  bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 && std::fwrite(&b->params, sizeof b->params, 1, fp) == 1 &&
+            std::fwrite(host.data(), 1, bytes, fp) == bytes;
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? FKK_OK : FKK_ERR_BAD_FILE;
+}
+
+fkk_status fkk_basis_load(fkk_ctx* ctx, const char* path, fkk_basis** out) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!path || !out) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_load: null argument");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(ctx, FKK_ERR_BAD_FILE, "fkk_basis_load: cannot open %s", path);
+  FileHead h{};
+  fkk_fit_params p{};
+  auto bad = [&](const char* why) {
+    std::fclose(fp);
+    return fail(ctx, FKK_ERR_BAD_FILE, "fkk_basis_load: %s", why);
+  };
+  if (std::fread(&h, sizeof h, 1, fp) != 1) return bad("truncated header");
+  if (std::memcmp(h.magic, kMagic, 8) != 0) return bad("not a basis file");
+  if (h.version != kFormat) return bad("unsupported format version");
+  if (h.params_size != sizeof(fkk_fit_params)) return bad("parameter block of another layout");
+  if (h.m < 2 || h.m > 2048 || h.k < 1 || h.k > 80 || h.k > h.m) return bad("sizes out of range");
+  if (h.block_bytes != basis_block_bytes(h.m, h.k)) return bad("block size does not match m and k");
+  if (std::fread(&p, sizeof p, 1, fp) != 1) return bad("truncated parameters");
+  std::vector<uint8_t> host(h.block_bytes);
+  if (std::fread(host.data(), 1, h.block_bytes, fp) != h.block_bytes) return bad("truncated data");
+  std::fclose(fp);
+  if (fnv1a(host.data(), host.size()) != h.checksum) return fail(ctx, FKK_ERR_BAD_FILE, "fkk_basis_load: checksum mismatch");
+  if (p.k != h.k) return fail(ctx, FKK_ERR_BAD_FILE, "fkk_basis_load: parameters disagree with the header");
+  FKK_TRY(bind(ctx));
+  fkk_status s;
+  fkk_basis* B = basis_alloc(ctx, h.m, h.k, &s);
+  if (!B) return s;
+  B->params = p;
+  B->L = h.L;
+  const cudaError_t e = cudaMemcpy(B->block, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(B->block);
+    delete B;
+    return cuda_check(ctx, e, "fkk_basis_load: upload");
+  }
   *out = B;
   return FKK_OK;
 }
