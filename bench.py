@@ -58,6 +58,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The slowest rank's time (each rank fits its own image, so the job's
+    throughput is the units of all ranks over this time)."""
+    import torch
+
+    if not dist:
+        return ms
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_per_rank, ms):
+    """Spectra per second of the whole job: every rank's n over the max time."""
+    return world * n_per_rank / (ms / 1e3)
+
+
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
@@ -289,11 +306,8 @@ def run_ours(args, rank, world, local):
     ctx.set_timing(False)
     for b in bases:
         b.close()
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * n / (ms_step / 1e3)
+    ms_step = max_over_ranks(ms_step, dist)
+    value = job_throughput(world, n, ms_step)
 
     # ---- roofline of the dominant stage ----
     pk = peaks()
@@ -392,12 +406,83 @@ def run_ours(args, rank, world, local):
                                    "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9}
         line["apply"] = {"value": n / (ap_ms / 1e3), "unit": "spectra/s", "ms": ap_ms,
                          "hbm_gbs": 8.0 * n * m / (ap_ms / 1e3) / 1e9}
+        line["serve"] = serve_leg(fk, ctx)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(cube)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serve_leg(fk, ctx, seconds=1.0):
+    """Serving of a trained basis (train 400 x 500 x 1,000, k = 40): tiles
+    of U{1,000..50,000} spectra cut from a new image of the same scene, in
+    pinned host memory, arriving as a Poisson process at 50,000 spectra/s,
+    then all at once (saturation).  Latency is submit -> completion."""
+    import numpy as np
+    import torch
+
+    from paper_2005_07132_gb300.synth import CONFIGS, Scene, make_cube
+
+    spec = CONFIGS["train400x500_m1000"]
+    scene = Scene.from_spec(spec)
+    train = make_cube(spec, image=0, scene=scene)
+    new = make_cube(spec, image=1, scene=scene)
+    x = torch.from_numpy(train.i_cars).cuda()
+    ref = torch.from_numpy(train.i_ref).cuda()
+    basis, _, _ = fk.fkk_fit_basis(ctx, x, ref, fk.fit_params(k=K_BASIS))
+    del x
+    pool = torch.from_numpy(new.i_cars).pin_memory()
+    outp = torch.empty_like(pool).pin_memory()
+    n_pool = pool.shape[0]
+    rng = np.random.default_rng(4)
+
+    def tiles(total):
+        out, pos, used = [], 0, 0
+        while used < total:
+            t = int(rng.integers(1000, 50001))
+            if pos + t > n_pool:
+                pos = 0
+            out.append((pos, t))
+            pos += t
+            used += t
+        return out
+
+    res = {"tile_sizes": "U{1000..50000}", "input": "pinned host", "train": "400x500x1000, k=40"}
+
+    def poisson(rate, secs):
+        # Poisson arrivals at `rate` spectra/s for about `secs` seconds
+        srv = fk.Server(ctx, basis)
+        plan = tiles(int(rate * secs))
+        gaps = rng.exponential([t / rate for _, t in plan])
+        ids = []
+        due = time.perf_counter()
+        for (pos, t), g in zip(plan, gaps):
+            due += g
+            while time.perf_counter() < due:
+                pass
+            ids.append(srv.submit(pool[pos:pos + t], outp[pos:pos + t]))
+        for rid in ids:
+            srv.wait(rid)
+        st = srv.stats()
+        st["requests"] = len(ids)
+        srv.stop()
+        return st
+
+    res["poisson_50k_per_s"] = poisson(50_000, 6.0 * seconds)
+    res["poisson_5M_per_s"] = poisson(5_000_000, 1.0 * seconds)
+    # saturation: everything queued at once
+    srv = fk.Server(ctx, basis)
+    plan = tiles(int(600_000))
+    ids = [srv.submit(pool[pos:pos + t], outp[pos:pos + t]) for pos, t in plan]
+    for rid in ids:
+        srv.wait(rid)
+    res["saturation"] = srv.stats()
+    res["saturation"]["requests"] = len(ids)
+    srv.stop()
+    basis.close()
+    return res
 
 
 def main():

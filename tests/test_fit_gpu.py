@@ -240,6 +240,20 @@ def test_fit_end_to_end_img64(fk, ctx, cube1, pec, sec):
     basis.close()
 
 
+@pytest.mark.parametrize("k", [20, 40, 80])
+def test_fit_precision_by_k(fk, ctx, cube1, k):
+    """rel-L2 of Im{K} against the fp64 oracle with PEC and SEC on, at
+    k = 20, 40 and 80 (the bound of the fp32-accurate path is 1e-4)."""
+    _, _, res = O.fit(cube1.i_cars, cube1.i_ref, O.FitParams(k=k))
+    basis, im, _ = fk.fkk_fit_basis(ctx, _dev(cube1.i_cars), _dev(cube1.i_ref), fk.fit_params(k=k))
+    st, _ = ctx.sync_status()
+    assert st == 0
+    err = rel_l2(im.cpu().numpy(), res["im"])
+    print(f"precision k={k}: rel-L2(Im) = {err:.3e}")
+    assert err <= 1e-4
+    basis.close()
+
+
 def test_fit_ragged_poisson_f(fk, ctx):
     """Odd channel count, N not a multiple of 64, k not a multiple of 8, and
     f(w) from the Poisson-Gaussian noise model (Sec. 2.2)."""
