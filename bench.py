@@ -353,7 +353,7 @@ def run_ours(args, rank, world, local):
                    "noise": "poisson+gauss snr20", "l2": "inputs (2.81 GB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "stage_ms": stage_acc,
-        "eig_phase_cycles": dict(zip(["load", "w", "pivot_reflector", "update", "barrier"], phases)),
+        "eig_phase_cycles": dict(zip(["load", "exchange_w", "pivot_reflector", "next_p", "deferred_update"], phases)),
         "device_status": int(status2), "clamped_ratios_per_fit": int(clamped) // max(1, max(3, args.warmup)),
         "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
     }

@@ -99,9 +99,11 @@ fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on);
 fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
 
 /* With timing on, the tridiagonal reduction of the last eigensolve records
- * the SM clock cycles its first CTA spent per phase, summed over the
- * columns: 0 loading and scaling G, 1 the vector w, 2 the pivot column and
- * the next reflector, 3 the update of the owned columns, 4 grid barriers.
+ * the SM clock cycles one CTA (the owner of the last column) spent per
+ * phase, summed over the columns: 0 loading and scaling G and the first
+ * reflector, 1 waiting for the exchanged p and pivot column and forming w,
+ * 2 the pivot column and the next reflector, 3 the next step's p of the
+ * owned columns (published), 4 the deferred update of the owned columns.
  * Copies n (<= 8) words. */
 fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n);
 

@@ -195,7 +195,7 @@ class Context:
 
     def eig_phase_cycles(self):
         """SM cycles per phase of the last timed tridiagonal reduction: load,
-        w, pivot column + reflector, column update, grid barriers."""
+        exchange + w, pivot column + reflector, next p, deferred update."""
         arr = (_I64 * 8)()
         self.check(lib().fkk_eig_phase_cycles(self._h, arr, 8), "fkk_eig_phase_cycles")
         return list(arr)[:5]

@@ -19,10 +19,13 @@
 // on the trailing rows/columns j+1..m-1.  Column c belongs to CTA c mod G and
 // stays in its shared memory (global memory when the matrix is too large);
 // warp s of a CTA updates its s-th column.  Every CTA forms the next
-// reflector itself: the owner of column j+1 has published that column before
-// the barrier, and with the full p every CTA can apply step j's update to it.
-// The dot products p of the next step are accumulated while the columns are
-// updated, so a step is one pass over the owned columns and one barrier.
+// reflector v' itself from the published pivot column and the full p.  The
+// p of the next step is then taken from the columns before this step's
+// update, corrected by the two scalars v.v' and w.v', and published; the
+// update itself follows while the other CTAs publish theirs.  So the
+// critical path of a step is the exchange, the reflector and one dot product
+// per column; there is no grid barrier (the exchanged words carry their step
+// in two tag bits).
 #include <algorithm>
 
 #include "common.cuh"
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     atomicMax(a.maxbits, __float_as_uint(t));
   }
   if (!grid_sync(a.bar, nb, target, a.abort_flag, a.status)) return;
-  mark(4);
+  mark(0);
   if (tid == 0) {
     const float t = __uint_as_float(__ldcg(a.maxbits));
     ex_s = t > 0.f ? ilogbf(t) : 0;
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     }
   }
   df tau_cur = sc[0];
+  df scal_cur = sc[2];  // v of step 0 is already scaled
   mark(0);
 
   const int nsteps = m - 2;
@@ -289,11 +293,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     const unsigned long long* pb = a.pbuf + (size_t)buf * m;
     const unsigned long long* cb = a.cbuf + (size_t)buf * m;
     const bool last = (j + 1 > m - 3);
-    // A. gather p and the pivot column (rows >= j+1) as they arrive; p.v
+    // A. v of this step from the raw pivot column the previous step kept
+    //    (each vector thread scales its own entries); gather p and the pivot
+    //    column (rows >= j+1) as they arrive; p.v
     df cbr[kMaxPer];
     bool ok = true;
     df dot = dw::make(0.f);
     if (vecw) {
+      if (j > 0) {
+#pragma unroll
+        for (int r = 0; r < kMaxPer; ++r) {
+          const int i = tid + r * kVecThreads;
+          if (i < m) {
+            const df x = i <= j ? dw::make(0.f) : (i == j + 1 ? dw::make(1.f) : dw::mul(v[i], scal_cur));
+            v[i] = x;
+            if (writer) a.u[(size_t)j * m + i] = x;
+          }
+        }
+      }
       unsigned long long wp[kMaxPer], wcb[kMaxPer];
       ok = gather_tagged(pb, tid, kVecThreads, j + 1, m, want, wp, a.abort_flag, a.status) &&
            gather_tagged(cb, tid, kVecThreads, j + 1, m, want, wcb, a.abort_flag, a.status);
@@ -325,39 +342,53 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
     }
     __syncthreads();
     mark(1);
-    // B. w = p - halfk v; pivot column x = c - v w_{j+1} - w after this step;
-    //    the next reflector from x
+    // B. w = p - halfk v; pivot column x = c - v w_{j+1} - w after this
+    //    step's update, kept raw; the next reflector from x, with
+    //    alpha = v.v' and beta = w.v' (v' = e_{j+2} + scal x below row j+2)
     const df halfk = sc[4], wj1 = sc[5];
-    df sig = dw::make(0.f);
+    df sig = dw::make(0.f), vx = dw::make(0.f), wx = dw::make(0.f);
     if (vecw) {
 #pragma unroll
       for (int r = 0; r < kMaxPer; ++r) {
         const int i = tid + r * kVecThreads;
         if (i < m && i >= j + 1) {
-          const df wi = dw::fnma(halfk, v[i], w[i]);
+          const df vi = v[i];
+          const df wi = dw::fnma(halfk, vi, w[i]);
           w[i] = wi;
-          const df x = dw::sub(dw::fnma(v[i], wj1, cbr[r]), wi);
+          const df x = dw::sub(dw::fnma(vi, wj1, cbr[r]), wi);
           vn[i] = x;
           if (i == j + 1 && writer) a.d[j + 1] = x;
           if (last) {
             if (i == m - 1 && writer) a.e[m - 2] = x;
           } else if (i >= j + 3) {
             sig = dw::add(sig, dw::mul(x, x));
+            vx = dw::add(vx, dw::mul(vi, x));
+            wx = dw::add(wx, dw::mul(wi, x));
           }
         }
       }
     }
-    df tau_nxt = dw::make(0.f);
+    df tau_nxt = dw::make(0.f), scal = dw::make(0.f);
     if (!last) {
       if (vecw) {
         sig = dw::warp_sum(sig);
-        if (lane == 0) red[kVecWarps + warp] = sig;
+        vx = dw::warp_sum(vx);
+        wx = dw::warp_sum(wx);
+        if (lane == 0) {
+          red[warp] = sig;
+          red[kVecWarps + warp] = vx;
+          red[2 * kVecWarps + warp] = wx;
+        }
       }
       __syncthreads();
       if (warp == 0) {
-        const df t = sum_vec_partials(red + kVecWarps);
+        const df ts = sum_vec_partials(red);
+        const df tv = sum_vec_partials(red + kVecWarps);
+        const df tw = sum_vec_partials(red + 2 * kVecWarps);
         if (lane == 0) {
-          reflector(vn[j + 2], t, sc);
+          reflector(vn[j + 2], ts, sc);
+          sc[6] = dw::add(v[j + 2], dw::mul(sc[2], tv));
+          sc[7] = dw::add(w[j + 2], dw::mul(sc[2], tw));
           if (writer) {
             a.e[j + 1] = sc[1];
             a.tau[j + 1] = sc[0];
@@ -366,52 +397,65 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
       }
       __syncthreads();
       tau_nxt = sc[0];
-      const df scal = sc[2];
-      if (vecw)
-        for (int i = tid; i < m; i += kVecThreads) {
-          df x;
-          if (i < j + 2) x = dw::make(0.f);
-          else if (i == j + 2) x = dw::make(1.f);
-          else x = dw::mul(vn[i], scal);
-          vn[i] = x;
-          if (writer) a.u[(size_t)(j + 1) * m + i] = x;
-        }
+      scal = sc[2];
+    } else {
+      __syncthreads();
     }
-    __syncthreads();
     mark(2);
-    // C. warp s updates own column s (c >= j+2) on rows >= j+2, accumulates
-    //    p of the next step and publishes it (and the next pivot column)
+    // C1. p of the next step from the owned columns as they are before this
+    //     step's update:  A'v' = A v' - v (w.v') - w (v.v')  column by column,
+    //     A v' = A[j+2, c] + scal (A[j+3.., c] . x); published at once.  The
+    //     owner of column j+2 also publishes that column after the update.
     if (warp < nloc) {
       const int c = b + warp * nb;
       if (c >= j + 2) {
-        df* col = colp(warp);
+        const df* col = colp(warp);
         const df wc = w[c], vc = v[c];
-        df acc = dw::make(0.f);
-        const unsigned tagn = step_tag(j + 1);
-        unsigned long long* cnext = a.cbuf + (size_t)nxt * m;
-        for (int i = j + 2 + lane; i < m; i += 32) {
-          const df x = dw::sub(col[i], dw::add(dw::mul(v[i], wc), dw::mul(w[i], vc)));
-          col[i] = x;
-          if (!last) {
-            acc = dw::add(acc, dw::mul(x, vn[i]));
-            if (c == j + 2) st_relaxed_u64(cnext + i, pack_tag(x, tagn));
-          } else if (i == m - 1) {
-            a.d[m - 1] = x;  // c == m - 1 here
+        if (last) {
+          // c == m - 1: the last diagonal entry
+          if (lane == 0) a.d[m - 1] = dw::sub(col[m - 1], dw::add(dw::mul(v[m - 1], wc), dw::mul(w[m - 1], vc)));
+        } else {
+          const unsigned tagn = step_tag(j + 1);
+          df acc = dw::make(0.f);
+          if (c == j + 2) {
+            unsigned long long* cnext = a.cbuf + (size_t)nxt * m;
+            for (int i = j + 2 + lane; i < m; i += 32) {
+              const df y = col[i];
+              st_relaxed_u64(cnext + i, pack_tag(dw::sub(y, dw::add(dw::mul(v[i], wc), dw::mul(w[i], vc))), tagn));
+              if (i > j + 2) acc = dw::add(acc, dw::mul(y, vn[i]));
+            }
+          } else {
+            for (int i = j + 3 + lane; i < m; i += 32) acc = dw::add(acc, dw::mul(col[i], vn[i]));
           }
-        }
-        if (!last) {
           acc = dw::warp_sum(acc);
-          if (lane == 0) st_relaxed_u64(a.pbuf + (size_t)nxt * m + c, pack_tag(dw::mul(tau_nxt, acc), tagn));
+          if (lane == 0) {
+            const df av = dw::add(col[j + 2], dw::mul(scal, acc));
+            const df pc = dw::mul(tau_nxt, dw::sub(av, dw::add(dw::mul(wc, sc[6]), dw::mul(vc, sc[7]))));
+            st_relaxed_u64(a.pbuf + (size_t)nxt * m + c, pack_tag(pc, tagn));
+          }
         }
       }
     }
     mark(3);
     if (last) break;
+    // C2. this step's update of the owned columns c >= j+3 on rows >= j+3
+    //     (the rows the next steps read), while the other CTAs publish
+    if (warp < nloc) {
+      const int c = b + warp * nb;
+      if (c >= j + 3) {
+        df* col = colp(warp);
+        const df wc = w[c], vc = v[c];
+        for (int i = j + 3 + lane; i < m; i += 32)
+          col[i] = dw::sub(col[i], dw::add(dw::mul(v[i], wc), dw::mul(w[i], vc)));
+      }
+    }
+    mark(4);
     df* tmp = v;
     v = vn;
     vn = tmp;
     tau_cur = tau_nxt;
-    __syncthreads();  // the column updates read v, w, vn; the next step rewrites them
+    scal_cur = scal;
+    __syncthreads();  // the column passes read v, w, vn; the next step rewrites them
   }
   if (timed)
     for (int q = 0; q < 5; ++q) a.cycles[q] = cyc[q];
