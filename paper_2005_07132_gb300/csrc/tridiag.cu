@@ -39,7 +39,7 @@ using dw::df;
 
 constexpr int kTrThreads = 512;
 constexpr int kTrWarps = kTrThreads / 32;
-constexpr int kVecWarps = 8;  // warps that run the length-m vector phases
+constexpr int kVecWarps = kTrWarps;  // warps that run the length-m vector phases
 constexpr int kVecThreads = kVecWarps * 32;
 constexpr int kMaxLoc = kTrWarps;  // columns per CTA (one warp each): m <= kMaxLoc * grid
 constexpr int kWY = 32;            // reflectors per block in the back-transformation
@@ -82,9 +82,9 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   return v;
 }
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v));
 }
-constexpr int kMaxPer = 8;  // vector entries per vector thread: m <= kMaxPer * kVecThreads
+constexpr int kMaxPer = 4;  // vector entries per vector thread: m <= kMaxPer * kVecThreads
 
 // Loads the words at p[i], i = i0 + r * stride (r < kMaxPer, lo <= i < m),
 // all in flight at once, and re-polls those not yet carrying `tag` until
@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
   df* v = smd + (kSmem ? (size_t)a.ncol_max * m : 0);
   df* vn = v + m;
   df* w = vn + m;
-  df* red = w + m;   // [32]
-  df* sc = red + 32; // [8] scalars
+  df* red = w + m;   // [64]
+  df* sc = red + 64; // [8] scalars
   __shared__ float fmax_s[kTrWarps];
   __shared__ int ex_s;
   unsigned target = 0;
@@ -1207,7 +1207,7 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   if (nb < 1) nb = 1;
   const int ncol_max = (m + nb - 1) / nb;
   if (ncol_max > kMaxLoc) return fail(ctx, FKK_ERR_INVALID_ARG, "eigensolve: m = %d too large", m);
-  const size_t vec_bytes = (size_t)(3 * m + 32 + 8) * sizeof(df);
+  const size_t vec_bytes = (size_t)(3 * m + 64 + 8) * sizeof(df);
   const size_t smem_cols = (size_t)ncol_max * m * sizeof(df) + vec_bytes;
   const bool in_smem = smem_cols <= 200 * 1024;
   const size_t smem_tr = in_smem ? smem_cols : vec_bytes;
