@@ -301,11 +301,17 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     ms_step = e0.elapsed_time(e1) / args.steps
     stage_acc = ctx.stage_ms()  # last step's stages
-    phases = ctx.eig_phase_cycles()
     status2, _ = ctx.sync_status()
-    ctx.set_timing(False)
     for b in bases:
         b.close()
+    bases.clear()
+    # one more, untimed step with the eigensolver's phase clocks (reading
+    # the SM clock perturbs that kernel, so the timed steps do not)
+    ctx.set_timing(2)
+    step().close()
+    torch.cuda.synchronize()
+    phases = ctx.eig_phase_cycles()
+    ctx.set_timing(False)
     ms_step = max_over_ranks(ms_step, dist)
     value = job_throughput(world, n, ms_step)
 

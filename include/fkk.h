@@ -87,18 +87,19 @@ size_t fkk_workspace_bytes(const fkk_ctx* ctx);
  * FKK_ERR_NOT_CONVERGED), else FKK_OK.  `clamped` may be NULL. */
 fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped);
 
-/* Turn per-stage timing of fkk_fit_basis on (1) or off (0).  When on, each
- * fit records CUDA events on its stream at the boundaries of six stages:
- * 0 transform (log ratio, split, channel sums), 1 Gram, 2 eigensolve,
- * 3 projection and argmax/argmin, 4 basis math (fKK, fPEC, fSEC), 5
- * reconstruction. */
+/* Per-stage timing of fkk_fit_basis: 0 off; 1 on: each fit records CUDA
+ * events on its stream at the boundaries of six stages: 0 transform (log
+ * ratio, split, channel sums), 1 Gram, 2 eigensolve, 3 projection and
+ * argmax/argmin, 4 basis math (fKK, fPEC, fSEC), 5 reconstruction; 2: as 1,
+ * and the eigensolver's reduction also reads the SM clock at its phase
+ * boundaries (fkk_eig_phase_cycles), which slows that kernel somewhat. */
 fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on);
 
 /* Milliseconds of the first n (<= 6) stages of the last timed fit;
  * synchronises on its last event. */
 fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
 
-/* With timing on, the tridiagonal reduction of the last eigensolve records
+/* With timing level 2, the tridiagonal reduction of the last eigensolve records
  * the SM clock cycles one CTA (the owner of the last column) spent per
  * phase, summed over the columns: 0 loading and scaling G and the first
  * reflector, 1 waiting for the exchanged p and pivot column and forming w,

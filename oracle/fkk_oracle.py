@@ -134,6 +134,51 @@ def kk_per_spectrum(i_cars, i_ref, L: int | None = None, ratio_floor: float = 1e
 
 
 # ---------------------------------------------------------------------------
+# Sec. 2.1 / Fig. 1(a): the conventional per-spectrum workflow (KK, PEC, SEC)
+# ---------------------------------------------------------------------------
+
+
+def conventional_from_phase(a, phi, params: "FitParams", L: int | None = None):
+    """PEC and SEC of Eq. KCARS_from_K on each spectrum, given its log
+    amplitude a = 1/2 ln(I/I_ref) and KK phase phi = H{a}.
+
+    PEC: phi_err = D{phi} (the ALS baseline, the same detrending operator as
+    fPEC), K_pec = exp(a + H{phi_err}) exp(i (phi - phi_err)).
+    SEC: K_CARS = K_pec / M{Re K_pec}, M the trendline operator (the plain
+    mean for sec_mode "mean"); with sec off the divisor is 1.
+    Returns (Re K_CARS, Im K_CARS)."""
+    a = np.atleast_2d(np.asarray(a, F64))
+    phi = np.atleast_2d(np.asarray(phi, F64))
+    M = a.shape[-1]
+    if params.pec:
+        lam = params.als_lambda if params.als_lambda is not None else default_als_lambda(M)
+        phi_err = np.stack([als_baseline(r, lam, params.als_p, params.als_iters) for r in phi])
+        h_err = hilbert(phi_err, L)
+    else:
+        phi_err = np.zeros_like(phi)
+        h_err = np.zeros_like(phi)
+    amp = np.exp(a + h_err)
+    ph = phi - phi_err
+    re = amp * np.cos(ph)
+    im = amp * np.sin(ph)
+    if params.sec:
+        win = params.sg_window or default_sg_window(M)
+        div = trend(re, params.sec_mode, win, params.sg_order)
+    else:
+        div = np.ones_like(re)
+    return re / div, im / div
+
+
+def conventional(i_cars, i_ref, params: "FitParams", L: int | None = None):
+    """The conventional workflow of Fig. 1(a) (without its denoising SVD):
+    per-spectrum KK (Eq. K), then PEC and SEC (Eq. KCARS_from_K).
+    Returns (Re K_CARS, Im K_CARS)."""
+    a = log_ratio(i_cars, i_ref, None, params.ratio_floor)
+    phi = hilbert(a, L or params.pad_len or None)
+    return conventional_from_phase(a, phi, params, L or params.pad_len or None)
+
+
+# ---------------------------------------------------------------------------
 # Sec. 2.2 (heteroscedastic addendum): noise-normalising spectrum f(w)
 # ---------------------------------------------------------------------------
 

@@ -182,8 +182,10 @@ class Context:
         st = lib().fkk_sync_status(self._h, _stream(stream), C.byref(n))
         return st, n.value
 
-    def set_timing(self, on: bool = True):
-        self.check(lib().fkk_set_timing(self._h, 1 if on else 0), "fkk_set_timing")
+    def set_timing(self, on=True):
+        """0/False off, 1/True stage events, 2 also the eigensolver phase clocks."""
+        level = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        self.check(lib().fkk_set_timing(self._h, level), "fkk_set_timing")
 
     STAGES = ("transform", "gram", "eig", "project", "basis", "recon")
 

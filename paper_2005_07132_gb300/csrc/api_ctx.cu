@@ -142,7 +142,8 @@ fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped) {
 fkk_status fkk_set_timing(fkk_ctx* ctx, int32_t on) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  ctx->timing = on != 0;
+  if (on < 0 || on > 2) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_set_timing: level %d not in 0..2", on);
+  ctx->timing = on;
   ctx->ev_valid = false;
   return FKK_OK;
 }

@@ -34,7 +34,7 @@ struct fkk_ctx {
   std::map<std::string, Buf> ws;
   std::recursive_mutex mu;
   // optional per-stage timing of the fit (CUDA events on the fit's stream)
-  bool timing = false;
+  int timing = 0;  // 0 off, 1 stage events, 2 also the eigensolver phase clocks
   static constexpr int kStages = 6;  // transform, gram, eig, project, basis, recon
   cudaEvent_t ev[kStages + 1] = {};
   bool ev_valid = false;

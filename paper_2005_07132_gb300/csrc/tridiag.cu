@@ -1235,7 +1235,7 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   int* ex_dev = (int*)(scr + 48);
   {
     long long* cycles = nullptr;
-    if (ctx->timing) {
+    if (ctx->timing >= 2) {
       cycles = (long long*)workspace(ctx, "eig_phase_cycles", 8 * sizeof(long long), &s);
       if (!cycles) return s;
     }
