@@ -227,6 +227,35 @@ enum {
 fkk_status fkk_basis_get(const fkk_basis* basis, int32_t which, double* host_dst, size_t count);
 
 /* ------------------------------------------------------------------ */
+/* Conventional workflow: per-spectrum KK, PEC and SEC (Sec. 2.1)       */
+/* ------------------------------------------------------------------ */
+
+/* The conventional per-spectrum workflow of Fig. 1(a) (after its denoising
+ * step), Eq. KCARS_from_K, for every spectrum n:
+ *   a       = 1/2 ln max(I_CARS[n,:] / I_ref, ratio_floor),  phi = H{a}
+ *             (the discrete Hilbert transform of kk_per_spectrum)
+ *   phi_err = D{phi} if params->pec, else 0: the asymmetric least squares
+ *             baseline (second-difference penalty als_lambda, asymmetry
+ *             als_p, als_iters reweightings, weights starting at 1) -- the
+ *             same detrending operator fPEC uses
+ *   K_pec   = exp(a + H{phi_err}) exp(i (phi - phi_err))
+ *   K_CARS  = K_pec / M{Re K_pec} if params->sec, else K_pec; M is the
+ *             Savitzky-Golay trendline (sg_window, sg_order <= 2; the
+ *             polynomial of the first / last full window near the edges) or
+ *             the mean over the channels (sec_mode FKK_SEC_MEAN)
+ * im_out (required) and re_out (may be NULL) receive Im and Re K_CARS.
+ * Uses pad_len (power of two in [M, 4096]; 0 = nextpow2(2M)), pec, sec,
+ * als_*, sec_mode, sg_window, sg_order and ratio_floor of *params; the other
+ * fields are ignored.  n_channels in [8, 2048].  Device arrays, row-major,
+ * row strides ld / ld_out.  Works in chunks of spectra inside a context
+ * workspace of about 32 M bytes per spectrum of a chunk (a chunk is halved
+ * until it fits the context's budget).  Clamped ratios are counted as by
+ * kk_per_spectrum.  Asynchronous on `stream`. */
+fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels,
+                                     int64_t ld, const float* i_ref, const fkk_fit_params* params, float* im_out,
+                                     float* re_out, int64_t ld_out, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Pipeline steps, exposed for composition and step-by-step checking    */
 /* ------------------------------------------------------------------ */
 

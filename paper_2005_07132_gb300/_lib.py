@@ -52,6 +52,7 @@ SIGNATURES = {
     "fkk_workspace_bytes": (_SZ, [_P]),
     "fkk_sync_status": (_I32, [_P, _P, C.POINTER(_I64)]),
     "kk_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _I32, _F32, _P, _P, _I64, _P]),
+    "conventional_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, _P, _I64, _P]),
     "fkk_fit_params_default": (None, [_P]),
     "fkk_fit_params_size": (_SZ, []),
     "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
@@ -236,6 +237,28 @@ def kk_per_spectrum(ctx: Context, i_cars, i_ref, pad_len: int = 0, ratio_floor: 
     st = lib().kk_per_spectrum(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref), pad_len,
                                ratio_floor, _ptr(im_out), _ptr(re_out), im_out.stride(0), _stream(stream))
     ctx.check(st, "kk_per_spectrum")
+    return (im_out, re_out) if re_out is not None else im_out
+
+
+def conventional_per_spectrum(ctx: Context, i_cars, i_ref, params: "FitParams", im_out=None, re_out=None,
+                              stream=None):
+    """The conventional workflow, per-spectrum KK + PEC + SEC
+    (C: conventional_per_spectrum).  Returns im_out (and re_out)."""
+    import torch
+
+    _check_2d(i_cars, "i_cars")
+    n, m = i_cars.shape
+    if im_out is None:
+        im_out = torch.empty((n, m), dtype=torch.float32, device=i_cars.device)
+    _check_2d(im_out, "im_out")
+    if re_out is not None:
+        _check_2d(re_out, "re_out")
+        if re_out.stride(0) != im_out.stride(0):
+            raise ValueError("re_out and im_out must share the row stride")
+    st = lib().conventional_per_spectrum(ctx.handle, _ptr(i_cars), n, m, i_cars.stride(0), _ptr(i_ref),
+                                         C.byref(params), _ptr(im_out), _ptr(re_out), im_out.stride(0),
+                                         _stream(stream))
+    ctx.check(st, "conventional_per_spectrum")
     return (im_out, re_out) if re_out is not None else im_out
 
 

@@ -1,0 +1,521 @@
+// The conventional per-spectrum workflow (Sec. 2.1 and Fig. 1(a) after its
+// denoising step; Eq. KCARS_from_K), the baseline the factorised method is
+// measured against:
+//   a       = 1/2 ln max(I/I_ref, floor),  phi = H{a}              (Eq. K)
+//   phi_err = D{phi}, the asymmetric-least-squares baseline         (PEC)
+//   K_pec   = exp(a + H{phi_err}) exp(i (phi - phi_err))
+//   K_CARS  = K_pec / M{Re K_pec}, M the trendline (or the mean)    (SEC)
+//
+// Spectra are processed in chunks.  Per chunk:
+//   1. the paired-FFT KK kernel in its phase mode writes phi (row-major);
+//   2. als_kernel runs the detrend with one thread per spectrum: each of the
+//      reweighting iterations solves (W + lam D2^T D2) z = W y, a symmetric
+//      pentadiagonal system, by a banded LDL^T forward sweep (storing the
+//      factor columns l1, l2 and D^-1 L^-1 W y) and a backward sweep (which
+//      also records the new weights as bits).  The system's condition number
+//      reaches 1e7 (lam up to ~1e5 against weights of 1e-2), so the solves run
+//      in double-word arithmetic; the 32 spectra of a warp go through shared
+//      memory tiles so that every global access of the sweeps is coalesced;
+//   3. conv_finish_kernel forms H{phi_err} (paired FFT), K_pec and the
+//      trendline of Re K_pec per spectrum (Savitzky-Golay of order <= 2 from
+//      fp64 prefix sums of x, i x, i^2 x, with the first / last full window's
+//      polynomial at the edges; or the mean) and writes Im (and Re) K_CARS.
+#include <algorithm>
+#include <cmath>
+
+#include "df64.cuh"
+#include "fft.cuh"
+#include "fit.h"
+#include "fkk_internal.h"
+
+namespace fkk {
+namespace {
+
+using dw::df;
+
+// ------------------------------------------------------------------- ALS ---
+
+constexpr int kAlsThreads = 128;
+constexpr int kAlsWarps = kAlsThreads / 32;
+
+struct AlsArgs {
+  const float* phi;  // n x m row-major (row stride m): the signal y of each spectrum
+  float* perr;       // n x m row-major: the baseline z of the last iteration
+  float* fac;        // [m][6][ns]: l1, l2, h (double-word) of the forward sweep
+  unsigned* bits;    // [ceil(m/32)][ns]: bit r of word b = (y > z) at row 32 b + r
+  int64_t n;         // spectra
+  int64_t ns;        // interleave stride: >= n, a multiple of 32
+  int m;
+  double lam, p;
+  int iters;
+};
+
+// Coefficients of D2^T D2 (D2 the (m-2) x m second-difference operator):
+// diagonal 1, 5, 6, ..., 6, 5, 1 and first off-diagonal -2, -4, ..., -4, -2
+// (general m >= 3); the second off-diagonal is 1.
+__device__ __forceinline__ float dtd0(int i, int m) {
+  return (i <= m - 3 ? 1.f : 0.f) + (i >= 1 && i <= m - 2 ? 4.f : 0.f) + (i >= 2 ? 1.f : 0.f);
+}
+__device__ __forceinline__ float dtd1(int i, int m) {  // entry (i, i+1)
+  return (i <= m - 3 ? -2.f : 0.f) + (i >= 1 && i <= m - 2 ? -2.f : 0.f);
+}
+
+__global__ void __launch_bounds__(kAlsThreads) als_kernel(AlsArgs a) {
+  __shared__ float tiles[kAlsWarps][32][33];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kAlsThreads + wib * 32;  // the warp's first spectrum
+  if (base >= a.n) return;  // no block-wide barrier below: a warp may leave
+  float(*T)[33] = tiles[wib];
+  const int64_t s = base + lane;
+  const bool live = s < a.n;
+  const int m = a.m, nblk = (m + 31) / 32;
+  const int64_t ns = a.ns;
+  const df lam = dw::from_double(a.lam);
+  const df pw = dw::from_double(a.p), qw = dw::from_double(1.0 - a.p), one = dw::make(1.f);
+
+  // T[q][r] = y of spectrum base + q at row 32 rb + r (0 outside)
+  auto load_tile = [&](int rb) {
+    __syncwarp();
+    const int i = rb * 32 + lane;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      const int64_t sq = base + q;
+      T[q][lane] = (sq < a.n && i < m) ? __ldg(a.phi + sq * m + i) : 0.f;
+    }
+    __syncwarp();
+  };
+
+  for (int it = 0; it < a.iters; ++it) {
+    const bool last = it == a.iters - 1;
+    // forward: L D L^T = W + lam D2^T D2 and g = L^-1 W y, one row at a time.
+    // With c_i = l1_i d_{i-1}: l2_i = lam / d_{i-2}, c_i = lam t1_{i-1} -
+    // l2_i c_{i-1}, l1_i = c_i / d_{i-1}, d_i = w_i + lam t0_i - l1_i c_i -
+    // l2_i lam, g_i = w_i y_i - l1_i g_{i-1} - l2_i g_{i-2}.
+    df rd1 = dw::make(0.f), rd2 = dw::make(0.f), c1 = dw::make(0.f), g1 = dw::make(0.f), g2 = dw::make(0.f);
+    for (int rb = 0; rb < nblk; ++rb) {
+      load_tile(rb);
+      const unsigned wb = (it > 0 && live) ? a.bits[(int64_t)rb * ns + s] : 0u;
+      const int rows = min(32, m - rb * 32);
+#pragma unroll 1
+      for (int r = 0; r < rows; ++r) {
+        const int i = rb * 32 + r;
+        const float y = T[lane][r];
+        const df w = it == 0 ? one : (((wb >> r) & 1u) ? pw : qw);
+        const df l2 = i >= 2 ? dw::mul(lam, rd2) : dw::make(0.f);
+        df c = dw::make(0.f), l1 = dw::make(0.f);
+        if (i >= 1) {
+          c = dw::sub(dw::mul(lam, dtd1(i - 1, m)), dw::mul(l2, c1));
+          l1 = dw::mul(c, rd1);
+        }
+        const df d = dw::sub(dw::sub(dw::add(w, dw::mul(lam, dtd0(i, m))), dw::mul(l1, c)), dw::mul(l2, lam));
+        const df g = dw::sub(dw::sub(dw::mul(w, y), dw::mul(l1, g1)), dw::mul(l2, g2));
+        const df rd = dw::rcp(d);
+        const df h = dw::mul(g, rd);
+        if (live) {
+          float* f = a.fac + (int64_t)i * 6 * ns + s;
+          f[0] = l1.h;
+          f[ns] = l1.l;
+          f[2 * ns] = l2.h;
+          f[3 * ns] = l2.l;
+          f[4 * ns] = h.h;
+          f[5 * ns] = h.l;
+        }
+        rd2 = rd1;
+        rd1 = rd;
+        c1 = c;
+        g2 = g1;
+        g1 = g;
+      }
+    }
+    // backward: z_i = h_i - l1_{i+1} z_{i+1} - l2_{i+2} z_{i+2}; the next
+    // weights are p where y > z, else 1 - p
+    df z1 = dw::make(0.f), z2 = dw::make(0.f), l1n = dw::make(0.f), l2n1 = dw::make(0.f), l2n2 = dw::make(0.f);
+    for (int rb = nblk - 1; rb >= 0; --rb) {
+      load_tile(rb);
+      unsigned wb = 0;
+      const int rows = min(32, m - rb * 32);
+#pragma unroll 1
+      for (int r = rows - 1; r >= 0; --r) {
+        const int i = rb * 32 + r;
+        df l1 = dw::make(0.f), l2 = dw::make(0.f), h = dw::make(0.f);
+        if (live) {
+          const float* f = a.fac + (int64_t)i * 6 * ns + s;
+          l1 = dw::make(f[0], f[ns]);
+          l2 = dw::make(f[2 * ns], f[3 * ns]);
+          h = dw::make(f[4 * ns], f[5 * ns]);
+        }
+        const df z = dw::sub(dw::sub(h, dw::mul(l1n, z1)), dw::mul(l2n2, z2));
+        const float y = T[lane][r];
+        const df dyz = dw::sub(dw::make(y), z);
+        if (dyz.h > 0.f || (dyz.h == 0.f && dyz.l > 0.f)) wb |= 1u << r;
+        if (last) T[lane][r] = z.h + z.l;
+        l2n2 = l2n1;
+        l2n1 = l2;
+        l1n = l1;
+        z2 = z1;
+        z1 = z;
+      }
+      if (!last) {
+        if (live) a.bits[(int64_t)rb * ns + s] = wb;
+      } else {
+        __syncwarp();
+        const int i = rb * 32 + lane;
+        if (i < m)
+          for (int q = 0; q < 32; ++q) {
+            const int64_t sq = base + q;
+            if (sq < a.n) a.perr[sq * m + i] = T[q][lane];
+          }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- finish ---
+
+constexpr int kFinThreads = 256;
+
+struct FinArgs {
+  const float* i_cars;
+  int64_t ld;
+  const float* i_ref;
+  const float* phi;   // n x m, row stride m
+  const float* perr;  // n x m, row stride m (null: no PEC)
+  int64_t n;
+  int m, L;
+  float floor_;
+  int sec;            // 0 off, 1 Savitzky-Golay, 2 mean
+  int window;         // odd Savitzky-Golay window
+  double gi[9];       // inverse of the window's moment matrix sum_t t^(a+b), a, b <= order
+  float* im;
+  float* re;
+  int64_t ld_out;
+};
+
+// Per slot of tpf threads: an exclusive scan of (x_i, i x_i, i^2 x_i) in
+// fp64 over i < m, written as P[i] (P[0] = 0 ... P[m] = total) into
+// p0, p1, p2.  wsum: 3 doubles per warp of the slot.  Block-wide barriers.
+__device__ void slot_prefix3(const float* x, int m, int t0, int tpf, double* p0, double* p1, double* p2,
+                             double* wsum) {
+  const int seg = (m + tpf - 1) / tpf;
+  const int lo = min(m, t0 * seg), hi = min(m, lo + seg);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = lo; i < hi; ++i) {
+    const double v = x[i], di = i;
+    s0 += v;
+    s1 += di * v;
+    s2 += di * di * v;
+  }
+  // inclusive scan within the warp
+  const int lane = t0 & 31, w = t0 >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u0 = __shfl_up_sync(0xffffffffu, s0, o);
+    const double u1 = __shfl_up_sync(0xffffffffu, s1, o);
+    const double u2 = __shfl_up_sync(0xffffffffu, s2, o);
+    if (lane >= o) {
+      s0 += u0;
+      s1 += u1;
+      s2 += u2;
+    }
+  }
+  if (lane == 31) {
+    wsum[3 * w] = s0;
+    wsum[3 * w + 1] = s1;
+    wsum[3 * w + 2] = s2;
+  }
+  __syncthreads();
+  double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+  for (int q = 0; q < w; ++q) {
+    e0 += wsum[3 * q];
+    e1 += wsum[3 * q + 1];
+    e2 += wsum[3 * q + 2];
+  }
+  // exclusive prefix of this thread's segment
+  double r0 = e0 + __shfl_up_sync(0xffffffffu, s0, 1);
+  double r1 = e1 + __shfl_up_sync(0xffffffffu, s1, 1);
+  double r2 = e2 + __shfl_up_sync(0xffffffffu, s2, 1);
+  if (lane == 0) {
+    r0 = e0;
+    r1 = e1;
+    r2 = e2;
+  }
+  if (t0 == 0) {
+    p0[0] = 0.0;
+    p1[0] = 0.0;
+    p2[0] = 0.0;
+  }
+  for (int i = lo; i < hi; ++i) {
+    const double v = x[i], di = i;
+    r0 += v;
+    r1 += di * v;
+    r2 += di * di * v;
+    p0[i + 1] = r0;
+    p1[i + 1] = r1;
+    p2[i + 1] = r2;
+  }
+  __syncthreads();
+}
+
+// Value at offset u from the centre c of the window [lo, hi) of the
+// least-squares polynomial through x (order <= 2), from the prefix sums.
+__device__ __forceinline__ double window_poly(const double* p0, const double* p1, const double* p2, int lo, int hi,
+                                              double c, double u, const double* gi) {
+  const double q0 = p0[hi] - p0[lo], q1 = p1[hi] - p1[lo], q2 = p2[hi] - p2[lo];
+  const double m0 = q0, m1 = q1 - c * q0, m2 = q2 - 2.0 * c * q1 + c * c * q0;  // sum_t t^k x, t = i - c
+  const double a0 = gi[0] * m0 + gi[1] * m1 + gi[2] * m2;
+  const double a1 = gi[3] * m0 + gi[4] * m1 + gi[5] * m2;
+  const double a2 = gi[6] * m0 + gi[7] * m1 + gi[8] * m2;
+  return a0 + u * (a1 + u * a2);
+}
+
+__global__ void __launch_bounds__(kFinThreads) conv_finish_kernel(FinArgs p, int tpf) {
+  extern __shared__ float4 smem_raw[];
+  const int L = p.L, M = p.m;
+  const int nfft = blockDim.x / tpf, f = threadIdx.x / tpf, t0 = threadIdx.x % tpf;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* buf0 = tw + L + f * (2 * L);
+  float2* buf1 = buf0 + L;
+  double* dbase = reinterpret_cast<double*>(tw + L + nfft * 2 * L);
+  double* p0 = dbase + (size_t)f * 3 * (M + 1);
+  double* p1 = p0 + (M + 1);
+  double* p2 = p1 + (M + 1);
+  double* wsum = dbase + (size_t)nfft * 3 * (M + 1) + f * 3 * (kFinThreads / 32);
+  float* fbase = reinterpret_cast<float*>(dbase + (size_t)nfft * 3 * (M + 1) + nfft * 3 * (kFinThreads / 32));
+  float* sre = fbase + (size_t)f * 4 * M;  // Re K_pec of the two spectra, then Im
+  float* sim = sre + 2 * M;
+  const int left = (L - M) / 2;
+  const float invL = 1.0f / (float)L;
+  const int hw = p.window / 2;
+
+  fill_twiddles(tw, L);
+  const int64_t npairs = (p.n + 1) / 2;
+  for (int64_t bp = (int64_t)blockIdx.x * nfft; bp < npairs; bp += (int64_t)gridDim.x * nfft) {
+    __syncthreads();
+    const int64_t pr = bp + f;
+    const bool live = pr < npairs;
+    const int64_t n0 = 2 * pr, n1 = 2 * pr + 1;
+    const bool has1 = live && n1 < p.n;
+    // H{phi_err} of both spectra (one complex FFT)
+    const float2* hb = nullptr;
+    if (p.perr) {
+      for (int t = t0; t < L; t += tpf) {
+        const int j = min(max(t - left, 0), M - 1);
+        buf0[t] = make_float2(live ? p.perr[n0 * M + j] : 0.f, has1 ? p.perr[n1 * M + j] : 0.f);
+      }
+      __syncthreads();
+      const int cur = fft_block<-1>(buf0, buf1, L, tw, t0, tpf);
+      float2* X = cur ? buf1 : buf0;
+      float2* Y = cur ? buf0 : buf1;
+      for (int t = t0; t < L; t += tpf) X[t] = hilbert_mult(X[t], t, L);
+      __syncthreads();
+      const int cur2 = fft_block<+1>(X, Y, L, tw, t0, tpf);
+      hb = cur2 ? Y : X;
+    }
+    // K_pec of both spectra
+    for (int j = t0; j < M; j += tpf) {
+      const float r = p.i_ref[j];
+      for (int q = 0; q < 2; ++q) {
+        const bool ok = q == 0 ? live : has1;
+        float re = 0.f, im = 0.f;
+        if (ok) {
+          const int64_t nq = q == 0 ? n0 : n1;
+          float x = p.i_cars[nq * p.ld + j] / r;
+          if (!(x >= p.floor_)) x = p.floor_;
+          const float av = 0.5f * logf(x);
+          float hv = 0.f, pe = 0.f;
+          if (p.perr) {
+            const float2 hh = hb[left + j];
+            hv = (q == 0 ? hh.x : hh.y) * invL;
+            pe = p.perr[nq * M + j];
+          }
+          const float amp = expf(av + hv);
+          float sn, cs;
+          sincosf(p.phi[nq * M + j] - pe, &sn, &cs);
+          re = amp * cs;
+          im = amp * sn;
+        }
+        sre[q * M + j] = re;
+        sim[q * M + j] = im;
+      }
+    }
+    __syncthreads();
+    // SEC: divide by the trendline of Re K_pec (every slot walks the same
+    // barriers, live or not)
+    for (int q = 0; q < 2; ++q) {
+      const bool ok = q == 0 ? live : has1;
+      const float* x = sre + q * M;
+      double mean = 0.0;
+      if (p.sec) slot_prefix3(x, M, t0, tpf, p0, p1, p2, wsum);
+      if (p.sec == 2) mean = p0[M] / (double)M;
+      if (ok) {
+        const int64_t nq = q == 0 ? n0 : n1;
+        for (int j = t0; j < M; j += tpf) {
+          double tr = 1.0;
+          if (p.sec == 2) {
+            tr = mean;
+          } else if (p.sec == 1) {
+            if (j < hw) tr = window_poly(p0, p1, p2, 0, p.window, hw, j - hw, p.gi);
+            else if (j >= M - hw) tr = window_poly(p0, p1, p2, M - p.window, M, M - 1 - hw, j - (M - 1 - hw), p.gi);
+            else tr = window_poly(p0, p1, p2, j - hw, j + hw + 1, j, 0.0, p.gi);
+          }
+          const float inv = (float)(1.0 / tr);
+          p.im[nq * p.ld_out + j] = sim[q * M + j] * inv;
+          if (p.re) p.re[nq * p.ld_out + j] = x[j] * inv;
+        }
+      }
+      __syncthreads();  // the prefix arrays are rewritten for the second spectrum
+    }
+  }
+}
+
+// inverse of the (order+1) x (order+1) moment matrix of the window
+// t = -h..h, embedded in a 3 x 3 array (zeros beyond the order)
+bool window_moment_inverse(int window, int order, double* gi) {
+  const int h = window / 2, n = order + 1;
+  double g[3][6] = {};
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < n; ++c) {
+      double s = 0.0;
+      for (int t = -h; t <= h; ++t) s += std::pow((double)t, r + c);
+      g[r][c] = s;
+    }
+    g[r][n + r] = 1.0;
+  }
+  for (int c = 0; c < n; ++c) {  // Gauss-Jordan with partial pivoting
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(g[r][c]) > std::fabs(g[piv][c])) piv = r;
+    if (g[piv][c] == 0.0) return false;
+    for (int k = 0; k < 2 * n; ++k) std::swap(g[c][k], g[piv][k]);
+    const double d = g[c][c];
+    for (int k = 0; k < 2 * n; ++k) g[c][k] /= d;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double e = g[r][c];
+        for (int k = 0; k < 2 * n; ++k) g[r][k] -= e * g[c][k];
+      }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) gi[3 * r + c] = (r < n && c < n) ? g[r][n + c] : 0.0;
+  return true;
+}
+
+size_t finish_smem_bytes(int L, int M, int nfft) {
+  return sizeof(float2) * (size_t)L +
+         (size_t)nfft * (2 * L * sizeof(float2) + 3 * (M + 1) * sizeof(double) + 3 * (kFinThreads / 32) * sizeof(double) +
+                         4 * M * sizeof(float));
+}
+
+}  // namespace
+}  // namespace fkk
+
+using namespace fkk;
+
+extern "C" fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra,
+                                                int32_t n_channels, int64_t ld, const float* i_ref,
+                                                const fkk_fit_params* params, float* im_out, float* re_out,
+                                                int64_t ld_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const int m = n_channels;
+  if (!params || n_spectra < 0 || m < 8 || m > 2048 || ld < m || ld_out < m)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: bad sizes (n=%lld m=%d)", (long long)n_spectra, m);
+  const fkk_fit_params& pp = *params;
+  const int L = pp.pad_len ? pp.pad_len : next_pow2(2 * (int64_t)m);
+  if (L < m || L > 4096 || (L & (L - 1)))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: pad_len %d invalid for %d channels", L, m);
+  if (!(pp.ratio_floor > 0.f)) return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: ratio_floor must be > 0");
+  if (pp.pec && (!(pp.als_p > 0.0 && pp.als_p < 1.0) || pp.als_iters < 1 || pp.als_iters > 1000))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: bad ALS parameters");
+  int sec = 0, window = 3, order = 0;
+  double gi[9] = {};
+  if (pp.sec) {
+    if (pp.sec_mode == FKK_SEC_MEAN) {
+      sec = 2;
+    } else if (pp.sec_mode == FKK_SEC_SAVGOL) {
+      sec = 1;
+      window = pp.sg_window;
+      if (!window) {
+        window = m / 2;
+        if (window % 2 == 0) --window;
+        if (window < 3) window = 3;
+      }
+      order = pp.sg_order;
+      if (window % 2 == 0 || window > m || window <= order || order < 0 || order > 2)
+        return fail(ctx, FKK_ERR_INVALID_ARG,
+                    "conventional_per_spectrum: Savitzky-Golay window %d / order %d (orders 0-2 supported)", window,
+                    order);
+      if (!window_moment_inverse(window, order, gi))
+        return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: singular Savitzky-Golay moments");
+    } else {
+      return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: bad sec_mode");
+    }
+  }
+  if (n_spectra == 0) return FKK_OK;
+  if (!i_cars || !i_ref || !im_out) return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: null pointer");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  const double lam = pp.als_lambda > 0.0 ? pp.als_lambda : 1e4 * std::pow(m / 1000.0, 4);
+
+  // finish-kernel launch shape (as the KK kernel: one FFT per tpf threads)
+  int tpf = L / 8;
+  if (tpf > kFinThreads) tpf = kFinThreads;
+  if (tpf < 32) tpf = 32;
+  const int nfft = kFinThreads / tpf;
+  const size_t fsmem = finish_smem_bytes(L, m, nfft);
+  if (fsmem > 227 * 1024)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: %d channels need %zu B of shared memory", m, fsmem);
+  FKK_CUDA(ctx, cudaFuncSetAttribute(conv_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+  int per_sm = 0;
+  FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_finish_kernel, kFinThreads, fsmem));
+  if (per_sm < 1) per_sm = 1;
+
+  // chunk of spectra: enough threads for every SM, within the budget
+  const int nblk = (m + 31) / 32;
+  const size_t per_spec = (size_t)m * 4 * 2 + (pp.pec ? (size_t)m * 6 * 4 + (size_t)nblk * 4 : 0);
+  int64_t chunk = std::min<int64_t>((n_spectra + 31) / 32 * 32, (int64_t)ctx->sm_count * 1024);
+  float* phi = nullptr;
+  fkk_status s = FKK_OK;
+  for (;;) {
+    phi = (float*)workspace(ctx, "conv_ws", (size_t)chunk * per_spec, &s);
+    if (phi || s != FKK_ERR_BUDGET || chunk <= 32) break;
+    chunk = std::max<int64_t>(32, chunk / 2 / 32 * 32);
+    ctx->last_error.clear();
+  }
+  if (!phi) return s;
+  float* perr = phi + (size_t)chunk * m;
+  float* fac = perr + (size_t)chunk * m;
+  unsigned* bits = reinterpret_cast<unsigned*>(fac + (size_t)chunk * m * 6);
+
+  for (int64_t c0 = 0; c0 < n_spectra; c0 += chunk) {
+    const int64_t cn = std::min<int64_t>(chunk, n_spectra - c0);
+    const float* src = i_cars + c0 * ld;
+    FKK_TRY(launch_kk_phase(ctx, src, cn, m, ld, i_ref, L, pp.ratio_floor, phi, m, st));
+    if (pp.pec) {
+      AlsArgs aa{phi, perr, fac, bits, cn, chunk, m, lam, pp.als_p, pp.als_iters};
+      const unsigned grid = (unsigned)((cn + kAlsThreads - 1) / kAlsThreads);
+      FKK_COUNT_LAUNCH(); als_kernel<<<grid, kAlsThreads, 0, st>>>(aa);
+      FKK_CUDA(ctx, cudaGetLastError());
+    }
+    FinArgs fa{};
+    fa.i_cars = src;
+    fa.ld = ld;
+    fa.i_ref = i_ref;
+    fa.phi = phi;
+    fa.perr = pp.pec ? perr : nullptr;
+    fa.n = cn;
+    fa.m = m;
+    fa.L = L;
+    fa.floor_ = pp.ratio_floor;
+    fa.sec = sec;
+    fa.window = window;
+    for (int q = 0; q < 9; ++q) fa.gi[q] = gi[q];
+    fa.im = im_out + c0 * ld_out;
+    fa.re = re_out ? re_out + c0 * ld_out : nullptr;
+    fa.ld_out = ld_out;
+    const int64_t npairs = (cn + 1) / 2;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((npairs + nfft - 1) / nfft, (int64_t)ctx->sm_count * per_sm));
+    FKK_COUNT_LAUNCH(); conv_finish_kernel<<<(unsigned)grid, kFinThreads, fsmem, st>>>(fa, tpf);
+    FKK_CUDA(ctx, cudaGetLastError());
+  }
+  return FKK_OK;
+}

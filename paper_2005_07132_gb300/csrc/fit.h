@@ -116,6 +116,12 @@ fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n
                                          int64_t ld_out, cudaStream_t st, void* p_hi, void* p_lo, void* c_hi,
                                          void* c_lo);
 
+// The per-spectrum KK kernel in its phase mode: phi = H{1/2 ln max(I/I_ref,
+// floor)} for n spectra, written with row stride ld_phi.
+fkk_status launch_kk_phase(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                           const float* i_ref, int L, float floor_, float* phi, int64_t ld_phi,
+                           cudaStream_t st);
+
 // Tensor map helper (driver entry point fetched once).
 fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,
                         uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,

@@ -7,7 +7,8 @@
 // to that of its (real) Hilbert transform, so the inverse FFT of
 // -i sgn(m) Z(m) is H{a0} + i H{a1}; no unpacking of the two spectra is
 // needed.  A block keeps its twiddle table in shared memory and walks
-// spectrum pairs in a grid-stride loop.
+// spectrum pairs in a grid-stride loop.  The same kernel, in its phase mode,
+// writes phi = H{a} itself for the conventional workflow's PEC.
 #include "fft.cuh"
 #include "fkk_internal.h"
 
@@ -30,6 +31,8 @@ struct KKArgs {
   long long* status;
 };
 
+// kPhase: write phi = H{a} to p.im (row stride p.ld_out) instead of Im/Re K.
+template <bool kPhase>
 __global__ void __launch_bounds__(kThreads) kk_pairs_kernel(KKArgs p, int tpf) {
   extern __shared__ float4 smem_raw[];
   const int L = p.L, M = p.m;
@@ -86,7 +89,13 @@ __global__ void __launch_bounds__(kThreads) kk_pairs_kernel(KKArgs p, int tpf) {
     __syncthreads();
     int cur2 = fft_block<+1>(X, Y, L, tw, t0, tpf);
     float2* H = cur2 ? Y : X;
-    if (live) {
+    if (live && kPhase) {
+      for (int j = t0; j < M; j += tpf) {
+        const float2 h = H[left + j];
+        p.im[n0 * p.ld_out + j] = h.x * invL;
+        if (has1) p.im[n1 * p.ld_out + j] = h.y * invL;
+      }
+    } else if (live) {
       for (int j = t0; j < M; j += tpf) {
         float2 h = H[left + j];
         float s0, c0;
@@ -117,26 +126,39 @@ static size_t kk_smem_bytes(int L, int M, int nfft) {
   return sizeof(float2) * (size_t)L + (size_t)nfft * (2 * L * sizeof(float2) + 2 * M * sizeof(float));
 }
 
-fkk_status launch_kk(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
-                     const float* i_ref, int L, float floor_, float* im, float* re,
-                     int64_t ld_out, cudaStream_t st) {
+template <bool kPhase>
+static fkk_status launch_kk_impl(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                                 const float* i_ref, int L, float floor_, float* im, float* re,
+                                 int64_t ld_out, cudaStream_t st) {
   int tpf = L / 8;
   if (tpf > kThreads) tpf = kThreads;
   if (tpf < 32) tpf = 32;
   int nfft = kThreads / tpf;
   size_t smem = kk_smem_bytes(L, m, nfft);
   if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "pad_len %d with %d channels needs %zu B of shared memory", L, m, smem);
-  FKK_CUDA(ctx, cudaFuncSetAttribute(kk_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FKK_CUDA(ctx, cudaFuncSetAttribute(kk_pairs_kernel<kPhase>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk_pairs_kernel, kThreads, smem));
+  FKK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk_pairs_kernel<kPhase>, kThreads, smem));
   if (per_sm < 1) per_sm = 1;
   int64_t npairs = (n + 1) / 2;
   int64_t want = (npairs + nfft - 1) / nfft;
   int64_t grid = std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm);
   if (grid < 1) grid = 1;
   KKArgs a{i_cars, n, m, ld, i_ref, L, floor_, im, re, ld_out, ctx->d_status};
-  FKK_COUNT_LAUNCH(); kk_pairs_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a, tpf);
+  FKK_COUNT_LAUNCH(); kk_pairs_kernel<kPhase><<<(unsigned)grid, kThreads, smem, st>>>(a, tpf);
   return cuda_check(ctx, cudaGetLastError(), "kk_pairs_kernel launch");
+}
+
+fkk_status launch_kk(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                     const float* i_ref, int L, float floor_, float* im, float* re,
+                     int64_t ld_out, cudaStream_t st) {
+  return launch_kk_impl<false>(ctx, i_cars, n, m, ld, i_ref, L, floor_, im, re, ld_out, st);
+}
+
+fkk_status launch_kk_phase(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
+                           const float* i_ref, int L, float floor_, float* phi, int64_t ld_phi,
+                           cudaStream_t st) {
+  return launch_kk_impl<true>(ctx, i_cars, n, m, ld, i_ref, L, floor_, phi, nullptr, ld_phi, st);
 }
 
 }  // namespace fkk
