@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / KK / apply / cpu baseline legs")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="cube of synth.CONFIGS to fit (the benchmark workload by default; a smaller one keeps "
+                         "profiler captures small)")
     return ap.parse_args()
 
 
@@ -196,7 +199,7 @@ def run_reference(args, rank, world):
     import oracle as O
     from paper_2005_07132_gb300.synth import CONFIGS, make_cube
 
-    cube = make_cube(CONFIGS[WORKLOAD])
+    cube = make_cube(CONFIGS[args.workload])
     n_sample = 50_000
     xi = cube.i_cars[:n_sample]
     f = O.noise_scale(cube.i_cars.astype(np.float64).mean(0), cube.alpha, cube.sigma_g)
@@ -215,7 +218,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_spectra": n_sample, "n_channels": int(cube.i_cars.shape[1]),
+        "config": {"workload": args.workload, "n_spectra": n_sample, "n_channels": int(cube.i_cars.shape[1]),
                    "k": K_BASIS, "sample": f"first {n_sample} spectra of the 703,026-spectrum cube"},
         "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores, "kind": "oracle",
                          "sample": f"fit of the first {n_sample} spectra (fp64 numpy oracle)"},
@@ -239,6 +242,20 @@ def cpu_baseline(cube):
                       f"({t:.1f} s)"}
 
 
+def conventional_cpu(cube, n_sample=300):
+    """The fp64 oracle's conventional workflow (KK, PEC, SEC per spectrum) on
+    the first n_sample spectra of the cube, one thread."""
+    import numpy as np
+
+    import oracle as O
+
+    t0 = time.perf_counter()
+    O.conventional(cube.i_cars[:n_sample].astype(np.float64), cube.i_ref.astype(np.float64), O.FitParams())
+    t = time.perf_counter() - t0
+    return {"value": n_sample / t, "unit": "spectra/s", "kind": "oracle",
+            "sample": f"fp64 oracle conventional workflow on the first {n_sample} spectra ({t:.1f} s)"}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -255,7 +272,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    spec = CONFIGS[WORKLOAD]
+    spec = CONFIGS[args.workload]
     cube = make_cube(spec, image=rank)  # each rank fits its own image of the scene
     n, m = cube.i_cars.shape
     ctx = fk.Context(local)
@@ -355,7 +372,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_spectra": n, "n_channels": m, "k": K_BASIS, "pec": True, "sec": True,
+        "config": {"workload": args.workload, "n_spectra": n, "n_channels": m, "k": K_BASIS, "pec": True, "sec": True,
                    "noise": "poisson+gauss snr20", "l2": "inputs (2.81 GB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "stage_ms": stage_acc,
@@ -415,9 +432,17 @@ def run_ours(args, rank, world, local):
                                    "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9}
         line["apply"] = {"value": n / (ap_ms / 1e3), "unit": "spectra/s", "ms": ap_ms,
                          "hbm_gbs": 8.0 * n * m / (ap_ms / 1e3) / 1e9}
+        # the conventional per-spectrum workflow (KK, ALS phase-error
+        # correction, Savitzky-Golay scale-error correction) the paper
+        # measures the factorised method against, on the same cube
+        cv_prm = fk.fit_params()
+        cv_ms = timed(lambda: fk.conventional_per_spectrum(ctx, x, ref, cv_prm, im_out=out, stream=st), reps=3)
+        line["conventional"] = {"value": n / (cv_ms / 1e3), "unit": "spectra/s", "ms": cv_ms,
+                                "steps": "KK + PEC (ALS, 20 reweightings) + SEC (Savitzky-Golay)"}
         line["serve"] = serve_leg(fk, ctx)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(cube)
+            line["conventional"]["cpu_oracle"] = conventional_cpu(cube)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

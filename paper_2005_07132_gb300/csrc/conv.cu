@@ -17,9 +17,10 @@
 //      in double-word arithmetic; the 32 spectra of a warp go through shared
 //      memory tiles so that every global access of the sweeps is coalesced;
 //   3. conv_finish_kernel forms H{phi_err} (paired FFT), K_pec and the
-//      trendline of Re K_pec per spectrum (Savitzky-Golay of order <= 2 from
-//      fp64 prefix sums of x, i x, i^2 x, with the first / last full window's
-//      polynomial at the edges; or the mean) and writes Im (and Re) K_CARS.
+//      trendline of Re K_pec per spectrum -- Savitzky-Golay of order <= 2 as
+//      the correlation with the centre-value kernel by a second paired FFT,
+//      with the first / last full window's polynomial at the edges; or the
+//      mean -- and writes Im (and Re) K_CARS.
 #include <algorithm>
 #include <cmath>
 
@@ -41,7 +42,7 @@ constexpr int kAlsWarps = kAlsThreads / 32;
 struct AlsArgs {
   const float* phi;  // n x m row-major (row stride m): the signal y of each spectrum
   float* perr;       // n x m row-major: the baseline z of the last iteration
-  float* fac;        // [m][6][ns]: l1, l2, h (double-word) of the forward sweep
+  float2* fac;       // [m][3][ns]: l1, l2, h (double-word) of the forward sweep
   unsigned* bits;    // [ceil(m/32)][ns]: bit r of word b = (y > z) at row 32 b + r
   int64_t n;         // spectra
   int64_t ns;        // interleave stride: >= n, a multiple of 32
@@ -60,7 +61,7 @@ __device__ __forceinline__ float dtd1(int i, int m) {  // entry (i, i+1)
   return (i <= m - 3 ? -2.f : 0.f) + (i >= 1 && i <= m - 2 ? -2.f : 0.f);
 }
 
-__global__ void __launch_bounds__(kAlsThreads) als_kernel(AlsArgs a) {
+__global__ void __launch_bounds__(kAlsThreads, 8) als_kernel(AlsArgs a) {
   __shared__ float tiles[kAlsWarps][32][33];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kAlsThreads + wib * 32;  // the warp's first spectrum
@@ -112,13 +113,10 @@ __global__ void __launch_bounds__(kAlsThreads) als_kernel(AlsArgs a) {
         const df rd = dw::rcp(d);
         const df h = dw::mul(g, rd);
         if (live) {
-          float* f = a.fac + (int64_t)i * 6 * ns + s;
-          f[0] = l1.h;
-          f[ns] = l1.l;
-          f[2 * ns] = l2.h;
-          f[3 * ns] = l2.l;
-          f[4 * ns] = h.h;
-          f[5 * ns] = h.l;
+          float2* f = a.fac + (int64_t)i * 3 * ns + s;
+          f[0] = make_float2(l1.h, l1.l);
+          f[ns] = make_float2(l2.h, l2.l);
+          f[2 * ns] = make_float2(h.h, h.l);
         }
         rd2 = rd1;
         rd1 = rd;
@@ -139,10 +137,11 @@ __global__ void __launch_bounds__(kAlsThreads) als_kernel(AlsArgs a) {
         const int i = rb * 32 + r;
         df l1 = dw::make(0.f), l2 = dw::make(0.f), h = dw::make(0.f);
         if (live) {
-          const float* f = a.fac + (int64_t)i * 6 * ns + s;
-          l1 = dw::make(f[0], f[ns]);
-          l2 = dw::make(f[2 * ns], f[3 * ns]);
-          h = dw::make(f[4 * ns], f[5 * ns]);
+          const float2* f = a.fac + (int64_t)i * 3 * ns + s;
+          const float2 f0 = f[0], f1 = f[ns], f2 = f[2 * ns];
+          l1 = dw::make(f0.x, f0.y);
+          l2 = dw::make(f1.x, f1.y);
+          h = dw::make(f2.x, f2.y);
         }
         const df z = dw::sub(dw::sub(h, dw::mul(l1n, z1)), dw::mul(l2n2, z2));
         const float y = T[lane][r];
@@ -173,6 +172,7 @@ __global__ void __launch_bounds__(kAlsThreads) als_kernel(AlsArgs a) {
 // ---------------------------------------------------------------- finish ---
 
 constexpr int kFinThreads = 256;
+constexpr int kFinWarps = kFinThreads / 32;
 
 struct FinArgs {
   const float* i_cars;
@@ -180,91 +180,45 @@ struct FinArgs {
   const float* i_ref;
   const float* phi;   // n x m, row stride m
   const float* perr;  // n x m, row stride m (null: no PEC)
+  const float* sgk;   // L: DFT of the Savitzky-Golay centre-value kernel (real)
   int64_t n;
   int m, L;
   float floor_;
   int sec;            // 0 off, 1 Savitzky-Golay, 2 mean
   int window;         // odd Savitzky-Golay window
-  double gi[9];       // inverse of the window's moment matrix sum_t t^(a+b), a, b <= order
+  float gi[9];        // inverse of the window's moment matrix sum_t t^(a+b), a, b <= order
   float* im;
   float* re;
   int64_t ld_out;
 };
 
-// Per slot of tpf threads: an exclusive scan of (x_i, i x_i, i^2 x_i) in
-// fp64 over i < m, written as P[i] (P[0] = 0 ... P[m] = total) into
-// p0, p1, p2.  wsum: 3 doubles per warp of the slot.  Block-wide barriers.
-__device__ void slot_prefix3(const float* x, int m, int t0, int tpf, double* p0, double* p1, double* p2,
-                             double* wsum) {
-  const int seg = (m + tpf - 1) / tpf;
-  const int lo = min(m, t0 * seg), hi = min(m, lo + seg);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int i = lo; i < hi; ++i) {
-    const double v = x[i], di = i;
-    s0 += v;
-    s1 += di * v;
-    s2 += di * di * v;
-  }
-  // inclusive scan within the warp
-  const int lane = t0 & 31, w = t0 >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    const double u0 = __shfl_up_sync(0xffffffffu, s0, o);
-    const double u1 = __shfl_up_sync(0xffffffffu, s1, o);
-    const double u2 = __shfl_up_sync(0xffffffffu, s2, o);
-    if (lane >= o) {
-      s0 += u0;
-      s1 += u1;
-      s2 += u2;
-    }
-  }
-  if (lane == 31) {
-    wsum[3 * w] = s0;
-    wsum[3 * w + 1] = s1;
-    wsum[3 * w + 2] = s2;
-  }
+// Sums v[0..11] over the tpf threads of a slot (whole warps); every thread
+// of the slot gets the totals.  red: kFinWarps * 12 floats per slot.
+// Block-wide barriers.
+__device__ void slot_sum12(float (&v)[12], int t0, int tpf, float* red) {
+#pragma unroll
+  for (int q = 0; q < 12; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((t0 & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) red[(t0 >> 5) * 12 + q] = v[q];
   __syncthreads();
-  double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-  for (int q = 0; q < w; ++q) {
-    e0 += wsum[3 * q];
-    e1 += wsum[3 * q + 1];
-    e2 += wsum[3 * q + 2];
-  }
-  // exclusive prefix of this thread's segment
-  double r0 = e0 + __shfl_up_sync(0xffffffffu, s0, 1);
-  double r1 = e1 + __shfl_up_sync(0xffffffffu, s1, 1);
-  double r2 = e2 + __shfl_up_sync(0xffffffffu, s2, 1);
-  if (lane == 0) {
-    r0 = e0;
-    r1 = e1;
-    r2 = e2;
-  }
-  if (t0 == 0) {
-    p0[0] = 0.0;
-    p1[0] = 0.0;
-    p2[0] = 0.0;
-  }
-  for (int i = lo; i < hi; ++i) {
-    const double v = x[i], di = i;
-    r0 += v;
-    r1 += di * v;
-    r2 += di * di * v;
-    p0[i + 1] = r0;
-    p1[i + 1] = r1;
-    p2[i + 1] = r2;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    float t = 0.f;
+    for (int w = 0; w < tpf / 32; ++w) t += red[w * 12 + q];
+    v[q] = t;
   }
   __syncthreads();
 }
 
-// Value at offset u from the centre c of the window [lo, hi) of the
-// least-squares polynomial through x (order <= 2), from the prefix sums.
-__device__ __forceinline__ double window_poly(const double* p0, const double* p1, const double* p2, int lo, int hi,
-                                              double c, double u, const double* gi) {
-  const double q0 = p0[hi] - p0[lo], q1 = p1[hi] - p1[lo], q2 = p2[hi] - p2[lo];
-  const double m0 = q0, m1 = q1 - c * q0, m2 = q2 - 2.0 * c * q1 + c * c * q0;  // sum_t t^k x, t = i - c
-  const double a0 = gi[0] * m0 + gi[1] * m1 + gi[2] * m2;
-  const double a1 = gi[3] * m0 + gi[4] * m1 + gi[5] * m2;
-  const double a2 = gi[6] * m0 + gi[7] * m1 + gi[8] * m2;
-  return a0 + u * (a1 + u * a2);
+// The fitted polynomial of a window at offset u from its centre, from the
+// window's moments m0..m2 about that centre.
+__device__ __forceinline__ float window_value(const float* gi, float m0, float m1, float m2, float u) {
+  const float c0 = gi[0] * m0 + gi[1] * m1 + gi[2] * m2;
+  const float c1 = gi[3] * m0 + gi[4] * m1 + gi[5] * m2;
+  const float c2 = gi[6] * m0 + gi[7] * m1 + gi[8] * m2;
+  return c0 + u * (c1 + u * c2);
 }
 
 __global__ void __launch_bounds__(kFinThreads) conv_finish_kernel(FinArgs p, int tpf) {
@@ -274,17 +228,13 @@ __global__ void __launch_bounds__(kFinThreads) conv_finish_kernel(FinArgs p, int
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* buf0 = tw + L + f * (2 * L);
   float2* buf1 = buf0 + L;
-  double* dbase = reinterpret_cast<double*>(tw + L + nfft * 2 * L);
-  double* p0 = dbase + (size_t)f * 3 * (M + 1);
-  double* p1 = p0 + (M + 1);
-  double* p2 = p1 + (M + 1);
-  double* wsum = dbase + (size_t)nfft * 3 * (M + 1) + f * 3 * (kFinThreads / 32);
-  float* fbase = reinterpret_cast<float*>(dbase + (size_t)nfft * 3 * (M + 1) + nfft * 3 * (kFinThreads / 32));
+  float* fbase = reinterpret_cast<float*>(tw + L + nfft * 2 * L);
   float* sre = fbase + (size_t)f * 4 * M;  // Re K_pec of the two spectra, then Im
   float* sim = sre + 2 * M;
+  float* red = fbase + (size_t)nfft * 4 * M + f * kFinWarps * 12;
   const int left = (L - M) / 2;
   const float invL = 1.0f / (float)L;
-  const int hw = p.window / 2;
+  const int W = p.window, hw = W / 2;
 
   fill_twiddles(tw, L);
   const int64_t npairs = (p.n + 1) / 2;
@@ -338,33 +288,85 @@ __global__ void __launch_bounds__(kFinThreads) conv_finish_kernel(FinArgs p, int
       }
     }
     __syncthreads();
-    // SEC: divide by the trendline of Re K_pec (every slot walks the same
-    // barriers, live or not)
+    // SEC: the trendline of Re K_pec.  Savitzky-Golay: the centre values are
+    // the correlation of Re K_pec with the centre-value kernel (an FFT pair,
+    // the two spectra in one complex transform, zero-padded so nothing
+    // wraps); near the edges, the polynomial of the first / last full window
+    // from its three moments.  Mean: the channel sum.
+    float mom[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) mom[q] = 0.f;
+    const float2* cb = nullptr;
+    if (p.sec == 1) {
+      for (int t = t0; t < L; t += tpf) buf0[t] = t < M ? make_float2(sre[t], sre[M + t]) : make_float2(0.f, 0.f);
+      for (int i = t0; i < W; i += tpf) {
+        const float u = (float)(i - hw);
+        const float xl0 = sre[i], xl1 = sre[M + i];
+        const float xh0 = sre[M - W + i], xh1 = sre[2 * M - W + i];
+        mom[0] += xl0;
+        mom[1] += u * xl0;
+        mom[2] += u * u * xl0;
+        mom[3] += xh0;
+        mom[4] += u * xh0;
+        mom[5] += u * u * xh0;
+        mom[6] += xl1;
+        mom[7] += u * xl1;
+        mom[8] += u * u * xl1;
+        mom[9] += xh1;
+        mom[10] += u * xh1;
+        mom[11] += u * u * xh1;
+      }
+      __syncthreads();
+      const int cur = fft_block<-1>(buf0, buf1, L, tw, t0, tpf);
+      float2* X = cur ? buf1 : buf0;
+      float2* Y = cur ? buf0 : buf1;
+      for (int t = t0; t < L; t += tpf) {
+        const float k = p.sgk[t];
+        X[t] = make_float2(X[t].x * k, X[t].y * k);
+      }
+      __syncthreads();
+      const int cur2 = fft_block<+1>(X, Y, L, tw, t0, tpf);
+      cb = cur2 ? Y : X;
+    } else if (p.sec == 2) {
+      for (int j = t0; j < M; j += tpf) {
+        mom[0] += sre[j];
+        mom[6] += sre[M + j];
+      }
+    }
+    if (p.sec) slot_sum12(mom, t0, tpf, red);
     for (int q = 0; q < 2; ++q) {
       const bool ok = q == 0 ? live : has1;
-      const float* x = sre + q * M;
-      double mean = 0.0;
-      if (p.sec) slot_prefix3(x, M, t0, tpf, p0, p1, p2, wsum);
-      if (p.sec == 2) mean = p0[M] / (double)M;
-      if (ok) {
-        const int64_t nq = q == 0 ? n0 : n1;
-        for (int j = t0; j < M; j += tpf) {
-          double tr = 1.0;
-          if (p.sec == 2) {
-            tr = mean;
-          } else if (p.sec == 1) {
-            if (j < hw) tr = window_poly(p0, p1, p2, 0, p.window, hw, j - hw, p.gi);
-            else if (j >= M - hw) tr = window_poly(p0, p1, p2, M - p.window, M, M - 1 - hw, j - (M - 1 - hw), p.gi);
-            else tr = window_poly(p0, p1, p2, j - hw, j + hw + 1, j, 0.0, p.gi);
-          }
-          const float inv = (float)(1.0 / tr);
-          p.im[nq * p.ld_out + j] = sim[q * M + j] * inv;
-          if (p.re) p.re[nq * p.ld_out + j] = x[j] * inv;
+      if (!ok) continue;
+      const int64_t nq = q == 0 ? n0 : n1;
+      const float* mq = mom + 6 * q;
+      for (int j = t0; j < M; j += tpf) {
+        float tr = 1.f;
+        if (p.sec == 2) {
+          tr = mq[0] / (float)M;
+        } else if (p.sec == 1) {
+          if (j < hw) tr = window_value(p.gi, mq[0], mq[1], mq[2], (float)(j - hw));
+          else if (j >= M - hw) tr = window_value(p.gi, mq[3], mq[4], mq[5], (float)(j - (M - 1 - hw)));
+          else tr = (q == 0 ? cb[j].x : cb[j].y) * invL;
         }
+        const float inv = 1.f / tr;
+        p.im[nq * p.ld_out + j] = sim[q * M + j] * inv;
+        if (p.re) p.re[nq * p.ld_out + j] = sre[q * M + j] * inv;
       }
-      __syncthreads();  // the prefix arrays are rewritten for the second spectrum
     }
   }
+}
+
+// DFT (length L) of the even Savitzky-Golay centre-value kernel
+// k(t) = g00 + g01 t + g02 t^2 on |t| <= h (zero elsewhere, t taken mod L).
+__global__ void sg_kernel_dft_kernel(int L, int h, double g00, double g01, double g02, float* out) {
+  const int mq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mq >= L) return;
+  double acc = 0.0;
+  for (int t = -h; t <= h; ++t) {
+    const long long mt = ((long long)mq * (t + L)) % L;
+    acc += (g00 + t * (g01 + t * g02)) * cospi(2.0 * (double)mt / (double)L);
+  }
+  out[mq] = (float)acc;
 }
 
 // inverse of the (order+1) x (order+1) moment matrix of the window
@@ -400,9 +402,8 @@ bool window_moment_inverse(int window, int order, double* gi) {
 }
 
 size_t finish_smem_bytes(int L, int M, int nfft) {
-  return sizeof(float2) * (size_t)L +
-         (size_t)nfft * (2 * L * sizeof(float2) + 3 * (M + 1) * sizeof(double) + 3 * (kFinThreads / 32) * sizeof(double) +
-                         4 * M * sizeof(float));
+  return sizeof(float2) * (size_t)L + (size_t)nfft * (2 * L * sizeof(float2) + 4 * M * sizeof(float)) +
+         (size_t)nfft * kFinWarps * 12 * sizeof(float);
 }
 
 }  // namespace
@@ -482,9 +483,16 @@ extern "C" fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_car
     ctx->last_error.clear();
   }
   if (!phi) return s;
+  float* sgk = nullptr;
+  if (sec == 1) {
+    sgk = (float*)workspace(ctx, "conv_sgk", (size_t)L * sizeof(float), &s);
+    if (!sgk) return s;
+    FKK_COUNT_LAUNCH(); sg_kernel_dft_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, window / 2, gi[0], gi[1], gi[2], sgk);
+    FKK_CUDA(ctx, cudaGetLastError());
+  }
   float* perr = phi + (size_t)chunk * m;
-  float* fac = perr + (size_t)chunk * m;
-  unsigned* bits = reinterpret_cast<unsigned*>(fac + (size_t)chunk * m * 6);
+  float2* fac = reinterpret_cast<float2*>(perr + (size_t)chunk * m);
+  unsigned* bits = reinterpret_cast<unsigned*>(fac + (size_t)chunk * m * 3);
 
   for (int64_t c0 = 0; c0 < n_spectra; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n_spectra - c0);
@@ -502,13 +510,14 @@ extern "C" fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_car
     fa.i_ref = i_ref;
     fa.phi = phi;
     fa.perr = pp.pec ? perr : nullptr;
+    fa.sgk = sgk;
     fa.n = cn;
     fa.m = m;
     fa.L = L;
     fa.floor_ = pp.ratio_floor;
     fa.sec = sec;
     fa.window = window;
-    for (int q = 0; q < 9; ++q) fa.gi[q] = gi[q];
+    for (int q = 0; q < 9; ++q) fa.gi[q] = (float)gi[q];
     fa.im = im_out + c0 * ld_out;
     fa.re = re_out ? re_out + c0 * ld_out : nullptr;
     fa.ld_out = ld_out;
