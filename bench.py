@@ -440,6 +440,7 @@ def run_ours(args, rank, world, local):
         line["conventional"] = {"value": n / (cv_ms / 1e3), "unit": "spectra/s", "ms": cv_ms,
                                 "steps": "KK + PEC (ALS, 20 reweightings) + SEC (Savitzky-Golay)"}
         line["serve"] = serve_leg(fk, ctx)
+        line["simulation"] = sim_leg(fk, ctx, st)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(cube)
             line["conventional"]["cpu_oracle"] = conventional_cpu(cube)
@@ -447,6 +448,62 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def sim_leg(fk, ctx, st, reps=3):
+    """The speed-enhancement curve of Sec. 4.1 on the simulation-shaped
+    workload (shape only: 74 x 246 base side-scaled by 0.5..4, 810 channels,
+    noiseless, three chemicals): the fKK-EC fit + reconstruction (k = 40,
+    PEC + SEC) against the conventional per-spectrum workflow, both on the
+    GPU, and the mean RSS of each against the known Im{chi / chi_nr} at side
+    scale 1 (a diagnostic, as in the paper's Fig. 2(e))."""
+    import numpy as np
+    import torch
+
+    from paper_2005_07132_gb300.synth import SIM_SIDE_SCALES, make_sim_cube
+
+    res = {"workload": "simulation-shaped, 74x246 base side-scaled, 810 channels, noiseless, 3 chemicals",
+           "k": 40, "points": []}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    prm = fk.fit_params(k=40)
+    cprm = fk.fit_params()
+    for side in SIM_SIDE_SCALES:
+        cube = make_sim_cube(side)
+        x = torch.from_numpy(cube.i_cars).cuda()
+        ref = torch.from_numpy(cube.i_ref).cuda()
+        out = torch.empty_like(x)
+        out2 = torch.empty_like(x)
+        fk.fkk_fit_basis(ctx, x, ref, prm, im_out=out, stream=st)[0].close()
+        bases = []
+        e0.record(st)
+        for _ in range(reps):
+            bases.append(fk.fkk_fit_basis(ctx, x, ref, prm, im_out=out, stream=st)[0])
+        e1.record(st)
+        torch.cuda.synchronize()
+        fit_ms = e0.elapsed_time(e1) / reps
+        for b in bases:
+            b.close()
+        fk.conventional_per_spectrum(ctx, x, ref, cprm, im_out=out2, stream=st)
+        e0.record(st)
+        for _ in range(reps):
+            fk.conventional_per_spectrum(ctx, x, ref, cprm, im_out=out2, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        conv_ms = e0.elapsed_time(e1) / reps
+        n = x.shape[0]
+        pt = {"side_scale": side, "n_spectra": n, "fit_ms": fit_ms, "conventional_ms": conv_ms,
+              "speed_enhancement": conv_ms / fit_ms}
+        if side == 1:
+            rows = np.arange(0, n, 7)
+            truth = cube.truth_im(rows)
+            r_t = torch.from_numpy(rows).cuda()
+            rss_f = float(np.mean(np.sum((out[r_t].cpu().numpy() - truth) ** 2, 1)))
+            rss_c = float(np.mean(np.sum((out2[r_t].cpu().numpy() - truth) ** 2, 1)))
+            pt["mean_rss"] = {"fkk_ec": rss_f, "conventional": rss_c, "null": float(np.mean(np.sum(truth**2, 1)))}
+        res["points"].append(pt)
+        del x, ref, out, out2
+    return res
 
 
 def serve_leg(fk, ctx, seconds=1.0):

@@ -140,7 +140,7 @@ enum { FKK_SEC_SAVGOL = 0, FKK_SEC_MEAN = 1 };
 enum { FKK_PREC_BF16X3 = 0 /* fp32-accurate: 3 bf16 products per term */ };
 
 typedef struct {
-  int32_t k;            /* kept basis vectors, 1..80 */
+  int32_t k;            /* kept basis vectors, 1..80; 0 = chosen by the rank rule (k_max, rank_eps) */
   int32_t pad_len;      /* Hilbert pad length: 0 = nextpow2(2M); power of two in [M, 4096] */
   int32_t pec;          /* 1 = factorised phase-error correction (Sec. 2.3) */
   int32_t sec;          /* 1 = factorised scale-error correction (Sec. 2.4) */
@@ -156,11 +156,20 @@ typedef struct {
   float ratio_floor;    /* I/I_ref is clamped to >= ratio_floor before the log (> 0) */
   double noise_alpha;   /* Poisson multiplier alpha of f(w) (Sec. 2.2); used when f is NULL */
   double noise_sigma_g; /* Gaussian sigma_g of f(w); alpha = sigma_g = 0 means f = 1 */
+  int32_t k_max;        /* k = 0: upper bound of the chosen k, 1..80 */
+  double rank_eps;      /* k = 0: the epsilon of the rank rule (> 0); 0 = FLT_EPSILON, the input's */
 } fkk_fit_params;
 
 /* Defaults: k 20, pad_len 0, pec 1, sec 1, als_lambda 0 (auto), als_p 0.01,
  * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
- * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0. */
+ * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
+ * k_max 80, rank_eps 0 (FLT_EPSILON).
+ *
+ * k = 0 selects the number of basis vectors by the rank rule of Sec. 4.1:
+ * the count of singular values s_i > s_1 * max(N, M) * rank_eps (the NumPy /
+ * MATLAB rank cutoff), computed from the k_max largest, at least 1.  The fit
+ * then reads k_max eigenvalues back to the host once (a synchronisation of
+ * `stream`), and the basis holds the chosen k (fkk_basis_info). */
 void fkk_fit_params_default(fkk_fit_params* p);
 
 /* Trained artefacts (Sec. 2.6: f, S, V, Phi_PEC, V_SEC) resident on the
@@ -169,7 +178,7 @@ typedef struct fkk_basis fkk_basis;
 
 /* Fit fKK-EC on a cube and optionally reconstruct it (Eq. fKKEC).
  *   A   = f(w) * 1/2 ln(max(I_CARS/I_ref, floor))       (Sec. 2.2, scaled A)
- *   A^T A = V diag(lambda) V^T (Jacobi eigensolve); s = sqrt(lambda_1..k);
+ *   A^T A = V diag(lambda) V^T (tridiagonal eigensolve); s = sqrt(lambda_1..k);
  *   P   = A V_k = U S;   q = argmax / argmin rows of each column of P
  *   fKK: B = V^T/f, H{B};  fPEC: Eq. phi_err_USphi_b + Eq. PEC_Ridge;
  *   fSEC: Eq. fSEC_VT;  Im{K} = exp(P C_amp) sin(P C_ph).
@@ -191,6 +200,18 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, i
  * NULL.  Errors: FKK_ERR_INVALID_ARG, FKK_ERR_BUDGET, FKK_ERR_CUDA. */
 fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* basis, const float* i_cars, int64_t n_spectra, int64_t ld,
                      float* im_out, float* re_out, int64_t ld_out, void* stream);
+
+/* Residual fraction of spectra on a trained basis -- whether the basis still
+ * supports new data (Sec. 1: readily testable; Sec. 5: retrain when it does
+ * not):  A = f * 1/2 ln(max(I/I_ref, floor)) with the basis' f, I_ref and
+ * floor, and
+ *   frac = ||A - A V V^T||_F^2 / ||A||_F^2 = 1 - ||A V||_F^2 / ||A||_F^2
+ * over the n spectra (V_k orthonormal).  On the training cube this equals
+ * 1 - sum(lambda_1..k) / energy (FKK_ART_ENERGY); a value well above that on
+ * new data means the data hold components the basis lacks.  Synchronises
+ * `stream`; *frac_out is written on the host. */
+fkk_status fkk_residual(fkk_ctx* ctx, const fkk_basis* basis, const float* i_cars, int64_t n_spectra, int64_t ld,
+                        double* frac_out, void* stream);
 
 /* Build a basis from HOST arrays (doubles): f (M), s (k), V (M x k), C_amp
  * and C_ph (k x M), I_ref (M).  params supplies k, pad_len, ratio_floor and
@@ -219,10 +240,13 @@ fkk_status fkk_basis_info(const fkk_basis* basis, int32_t* n_channels, int32_t* 
  *   FKK_ART_B, FKK_ART_H_B, FKK_ART_PHI_PEC, FKK_ART_H_PHI, FKK_ART_V_SEC,
  *   FKK_ART_C_AMP, FKK_ART_C_PH      k*M each, row-major k x M
  *   FKK_ART_Q        nq       sub-sampled row indices (sorted)
+ *   FKK_ART_ENERGY   1        ||A||_F^2 = trace(A^T A) of the training cube, so
+ *                             that 1 - sum(lambda) / energy is the training
+ *                             residual fraction (compare fkk_residual)
  * `count` must equal the element count. */
 enum {
   FKK_ART_S = 0, FKK_ART_LAMBDA, FKK_ART_V, FKK_ART_F, FKK_ART_B, FKK_ART_H_B, FKK_ART_PHI_PEC,
-  FKK_ART_H_PHI, FKK_ART_V_SEC, FKK_ART_C_AMP, FKK_ART_C_PH, FKK_ART_Q
+  FKK_ART_H_PHI, FKK_ART_V_SEC, FKK_ART_C_AMP, FKK_ART_C_PH, FKK_ART_Q, FKK_ART_ENERGY
 };
 fkk_status fkk_basis_get(const fkk_basis* basis, int32_t which, double* host_dst, size_t count);
 

@@ -62,6 +62,8 @@ class FitParams:
     sg_order: int = 2
     ml_lambda: float = 0.0
     ratio_floor: float = 1e-6
+    k_max: int = 80          # k = 0: the rank rule picks k <= k_max
+    rank_eps: float = 0.0    # epsilon of the rank rule; 0 -> float32 machine epsilon
 
 
 def pad_len(n_channels: int) -> int:
@@ -211,6 +213,26 @@ def eig_desc(G):
     sign = np.sign(V[idx, np.arange(V.shape[1])])
     sign[sign == 0] = 1.0
     return lam, V * sign
+
+
+def rank_k(lam, n: int, m: int, k_max: int, eps: float = 0.0) -> int:
+    """The rank rule of Sec. 4.1: the number of singular values s_i of A
+    (s = sqrt(lambda)) above s_1 * max(N, M) * eps, among the k_max largest
+    (at least 1).  eps = 0 means the float32 machine epsilon, the epsilon of
+    the input data type."""
+    eps = eps or float(np.finfo(np.float32).eps)
+    s = np.sqrt(np.maximum(np.asarray(lam, F64)[:k_max], 0.0))
+    tol = s[0] * max(n, m) * eps
+    return max(1, int(np.sum(s > tol)))
+
+
+def residual_fraction(basis: "Basis", i_new) -> float:
+    """||A - A V V^T||_F^2 / ||A||_F^2 of new spectra on a trained basis:
+    how much of the new data the basis does not represent (Sec. 5: retrain
+    when the basis vectors do not adequately support new data)."""
+    A = log_ratio(i_new, basis.i_ref, basis.f, basis.params.ratio_floor)
+    PV = A @ basis.V
+    return float(1.0 - np.sum(PV * PV) / np.sum(A * A))
 
 
 def singular_from_eig(lam) -> np.ndarray:
@@ -392,7 +414,6 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
     (all rows if None), the eigenvalues and q."""
     i_cars = np.asarray(i_cars)
     N, M = i_cars.shape
-    k = params.k
     L = params.pad_len or pad_len(M)
     f = np.ones(M) if f is None else np.asarray(f, F64)
     G = np.zeros((M, M))
@@ -400,6 +421,7 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
         A = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor)
         G += A.T @ A
     lam, Vall = eig_desc(G)
+    k = params.k or rank_k(lam, N, M, params.k_max, params.rank_eps)
     V = Vall[:, :k]
     s = singular_from_eig(lam[:k])
     P = np.empty((N, k))
@@ -407,10 +429,10 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
         P[a : a + chunk] = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor) @ V
     B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph, q = basis_math(V, P, f, params, L)
     basis = Basis(f, s, V, B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph,
-                  np.asarray(i_ref, F64), params, {"lam": lam, "q": q, "G": G})
+                  np.asarray(i_ref, F64), params, {"lam": lam, "q": q, "G": G, "k": k, "energy": float(np.trace(G))})
     rows = slice(None) if out_rows is None else out_rows
     re, im = reconstruct(P[rows], c_amp, c_ph)
-    return basis, P, {"re": re, "im": im, "lam": lam, "q": q}
+    return basis, P, {"re": re, "im": im, "lam": lam, "q": q, "k": k}
 
 
 def apply_projector(basis: Basis) -> np.ndarray:

@@ -28,6 +28,7 @@ from ._lib import (  # noqa: F401
     fkk_reconstruct_noalloc,
     kk_per_spectrum,
     conventional_per_spectrum,
+    fkk_residual,
     launch_count,
     lib,
     Server,
@@ -36,6 +37,6 @@ from ._lib import (  # noqa: F401
 __all__ = [
     "Basis", "Context", "FitParams", "FkkError", "SEC_MEAN", "SEC_SAVGOL", "fit_params", "fkk_apply",
     "fkk_basis_from_arrays", "fkk_basis_load", "fkk_noise_scale", "Server", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_gram", "fkk_project",
-    "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "conventional_per_spectrum",
+    "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "conventional_per_spectrum", "fkk_residual",
     "launch_count", "lib",
 ]

@@ -53,6 +53,7 @@ SIGNATURES = {
     "fkk_sync_status": (_I32, [_P, _P, C.POINTER(_I64)]),
     "kk_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _I32, _F32, _P, _P, _I64, _P]),
     "conventional_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, _P, _I64, _P]),
+    "fkk_residual": (_I32, [_P, _P, _P, _I64, _I64, C.POINTER(C.c_double), _P]),
     "fkk_fit_params_default": (None, [_P]),
     "fkk_fit_params_size": (_SZ, []),
     "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
@@ -87,12 +88,13 @@ class FitParams(C.Structure):
         ("ridge_rel", C.c_double), ("sec_mode", C.c_int32), ("sg_window", C.c_int32),
         ("sg_order", C.c_int32), ("ml_lambda", C.c_double), ("precision", C.c_int32),
         ("ratio_floor", C.c_float), ("noise_alpha", C.c_double), ("noise_sigma_g", C.c_double),
+        ("k_max", C.c_int32), ("rank_eps", C.c_double),
     ]
 
 
 SEC_SAVGOL, SEC_MEAN = 0, 1
 ART = {name: i for i, name in enumerate(
-    ["s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q"])}
+    ["s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q", "energy"])}
 
 
 def launch_count() -> int:
@@ -262,6 +264,16 @@ def conventional_per_spectrum(ctx: Context, i_cars, i_ref, params: "FitParams", 
     return (im_out, re_out) if re_out is not None else im_out
 
 
+def fkk_residual(ctx: Context, basis: "Basis", i_cars, stream=None) -> float:
+    """||A - A V V^T||^2 / ||A||^2 of the spectra on the basis (fkk_residual)."""
+    _check_2d(i_cars, "i_cars")
+    out = C.c_double(0.0)
+    st = lib().fkk_residual(ctx.handle, basis.handle, _ptr(i_cars), i_cars.shape[0], i_cars.stride(0),
+                            C.byref(out), _stream(stream))
+    ctx.check(st, "fkk_residual")
+    return out.value
+
+
 class Basis:
     """Owns an fkk_basis (fkk_basis_free on close)."""
 
@@ -280,13 +292,18 @@ class Basis:
             raise FkkError(st, "fkk_basis_info")
         return {"n_channels": m.value, "k": k.value, "pad_len": L.value, "nq": nq.value}
 
+    def training_residual(self) -> float:
+        """1 - sum(lambda_1..k) / ||A||_F^2 of the training cube: the residual
+        fraction fkk_residual returns on the training data itself."""
+        return float(1.0 - self.get("lambda").sum() / self.get("energy")[0])
+
     def get(self, which: str):
         """One artefact as a float64 numpy array (fkk_basis_get)."""
         import numpy as np
 
         inf = self.info()
         m, k, nq = inf["n_channels"], inf["k"], inf["nq"]
-        shape = {"s": (k,), "lambda": (k,), "v": (m, k), "f": (m,), "q": (nq,)}.get(which, (k, m))
+        shape = {"s": (k,), "lambda": (k,), "v": (m, k), "f": (m,), "q": (nq,), "energy": (1,)}.get(which, (k, m))
         out = np.empty(shape, np.float64)
         st = lib().fkk_basis_get(self._h, ART[which], out.ctypes.data_as(C.c_void_p), out.size)
         if st != FKK_OK:

@@ -1,11 +1,14 @@
 // C-ABI entry points of the fKK-EC fit, the ML apply, the basis object and
 // the individual pipeline steps (include/fkk.h).
+#include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
+#include "common.cuh"
 #include "fit.h"
 
 struct fkk_basis {
@@ -26,6 +29,7 @@ struct fkk_basis {
   double* c_ph = nullptr;
   int64_t* q = nullptr;     // up to 2k
   int* nq = nullptr;        // device count
+  double* energy = nullptr; // trace(A^T A) of the training cube (in the pad after nq)
   float* i_ref = nullptr;   // m
   void* block = nullptr;    // single allocation backing all of the above
 };
@@ -52,9 +56,71 @@ __global__ void copy_f32_kernel(const float* __restrict__ a, int m, float* __res
   if (j < m) b[j] = a[j];
 }
 
+// *out = trace(G), one block.
+__global__ void trace_kernel(const double* __restrict__ g, int m, double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) t += g[(int64_t)j * m + j];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+    *out = u;
+  }
+}
+
+// acc[0] += sum over rows of ||f a||^2 (a = 1/2 ln max(I/I_ref, floor)),
+// acc[1] += sum of P^2 (n x k).  A warp per row, fp64 block sums.
+__global__ void residual_energy_kernel(const float* __restrict__ i_cars, int64_t n, int m, int64_t ld,
+                                       const float* __restrict__ i_ref, float floor_, const double* __restrict__ f,
+                                       const float* __restrict__ p, int k, double* __restrict__ acc) {
+  __shared__ double red[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double ea = 0.0, ep = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < n; r += (int64_t)gridDim.x * nw) {
+    float sa = 0.f;
+    for (int j = lane; j < m; j += 32) {
+      float x = i_cars[r * ld + j] / i_ref[j];
+      if (!(x >= floor_)) x = floor_;
+      const float a = (float)f[j] * 0.5f * logf(x);
+      sa = fmaf(a, a, sa);
+    }
+    float sp = 0.f;
+    for (int i = lane; i < k; i += 32) {
+      const float v = p[r * k + i];
+      sp = fmaf(v, v, sp);
+    }
+    ea += sa;
+    ep += sp;
+  }
+  ea = warp_sum(ea);
+  ep = warp_sum(ep);
+  if (lane == 0) {
+    red[0][warp] = ea;
+    red[1][warp] = ep;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0, v = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      u += red[0][w];
+      v += red[1][w];
+    }
+    atomicAdd(acc, u);
+    atomicAdd(acc + 1, v);
+  }
+}
+
 fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n) {
-  if (p.k < 1 || p.k > 80 || p.k > m) return fail(ctx, FKK_ERR_INVALID_ARG, "k=%d must be in [1, min(80, M)]", p.k);
-  if (n < p.k) return fail(ctx, FKK_ERR_INVALID_ARG, "need at least k spectra");
+  if (p.k == 0) {
+    if (p.k_max < 1 || p.k_max > 80) return fail(ctx, FKK_ERR_INVALID_ARG, "k_max=%d must be in [1, 80]", p.k_max);
+    if (!(p.rank_eps >= 0.0)) return fail(ctx, FKK_ERR_INVALID_ARG, "rank_eps must be >= 0");
+  } else {
+    if (p.k < 1 || p.k > 80 || p.k > m) return fail(ctx, FKK_ERR_INVALID_ARG, "k=%d must be in [1, min(80, M)]", p.k);
+    if (n < p.k) return fail(ctx, FKK_ERR_INVALID_ARG, "need at least k spectra");
+  }
   if (p.pad_len && (p.pad_len < m || p.pad_len > 4096 || (p.pad_len & (p.pad_len - 1))))
     return fail(ctx, FKK_ERR_INVALID_ARG, "pad_len %d invalid", p.pad_len);
   if (!p.pad_len && next_pow2(2 * (int64_t)m) > 4096)
@@ -132,6 +198,7 @@ fkk_basis* basis_alloc(fkk_ctx* ctx, int m, int k, fkk_status* st) {
   b->c_ph = d; d += mk;
   b->q = (int64_t*)d;
   b->nq = (int*)(b->q + 2 * k);
+  b->energy = reinterpret_cast<double*>(b->nq) + 1;
   b->i_ref = (float*)(reinterpret_cast<uint8_t*>(b->nq) + 64);
   b->device = ctx->device;
   b->m = m;
@@ -166,6 +233,8 @@ void fkk_fit_params_default(fkk_fit_params* p) {
   p->ratio_floor = 1e-6f;
   p->noise_alpha = 0.0;
   p->noise_sigma_g = 0.0;
+  p->k_max = 80;
+  p->rank_eps = 0.0;
 }
 
 fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
@@ -179,40 +248,79 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   FKK_TRY(check_params(ctx, *params, m, n));
   FKK_TRY(bind(ctx));
   cudaStream_t st = as_stream(stream);
-  const fkk_fit_params& p = *params;
-  const int k = p.k;
+  fkk_fit_params p = *params;  // k is filled in below when chosen by the rank rule
+  const bool autok = p.k == 0;
+  int k = p.k;
   const int L = p.pad_len ? p.pad_len : next_pow2(2 * (int64_t)m);
   fkk_status s;
-  fkk_basis* B = basis_alloc(ctx, m, k, &s);
-  if (!B) return s;
-  B->params = p;
-  B->L = L;
+  fkk_basis* B = nullptr;
   auto bail = [&](fkk_status e) {
     cudaStreamSynchronize(st);
-    cudaFree(B->block);
-    delete B;
+    if (B) {
+      cudaFree(B->block);
+      delete B;
+    }
     return e;
   };
+  double* f_dev = nullptr;  // f(w): the basis' own array, or a workspace until k is known
+  if (autok) {
+    f_dev = (double*)workspace(ctx, "fit_f_auto", (size_t)m * 8, &s);
+    if (!f_dev) return s;
+  } else {
+    B = basis_alloc(ctx, m, k, &s);
+    if (!B) return s;
+    f_dev = B->f;
+  }
   DtLayout D;
   stage_mark(ctx, 0, st);
   s = launch_transform(ctx, i_cars, n, m, ld, i_ref, p.ratio_floor, D, st);
   if (s) return bail(s);
   // f(w)
   if (f_or_null) {
-    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(f_or_null, m, B->f);
+    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(f_or_null, m, f_dev);
   } else if (p.noise_alpha > 0.0 || p.noise_sigma_g > 0.0) {
-    s = launch_noise_scale(ctx, D.sum_i, n, m, p.noise_alpha, p.noise_sigma_g, B->f, st);
+    s = launch_noise_scale(ctx, D.sum_i, n, m, p.noise_alpha, p.noise_sigma_g, f_dev, st);
     if (s) return bail(s);
   } else {
-    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(nullptr, m, B->f);
+    FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(nullptr, m, f_dev);
   }
-  FKK_COUNT_LAUNCH(); copy_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_ref, m, B->i_ref);
   double* G = (double*)workspace(ctx, "fit_gram", (size_t)m * m * 8, &s);
   if (!G) return bail(s);
   stage_mark(ctx, 1, st);
-  if ((s = launch_gram(ctx, D, B->f, G, st))) return bail(s);
+  if ((s = launch_gram(ctx, D, f_dev, G, st))) return bail(s);
   stage_mark(ctx, 2, st);
-  if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
+  if (autok) {
+    // the k_max largest eigenpairs, then the rank rule on the host
+    const int kmax = std::min(p.k_max, m);
+    double* lam_a = (double*)workspace(ctx, "fit_lam_auto", (size_t)kmax * 8, &s);
+    if (!lam_a) return bail(s);
+    double* v_a = (double*)workspace(ctx, "fit_v_auto", (size_t)m * kmax * 8, &s);
+    if (!v_a) return bail(s);
+    if ((s = launch_eig_topk(ctx, G, m, kmax, lam_a, v_a, st))) return bail(s);
+    std::vector<double> lam(kmax);
+    if ((s = cuda_check(ctx, cudaMemcpyAsync(lam.data(), lam_a, kmax * 8, cudaMemcpyDeviceToHost, st), "lambda")))
+      return bail(s);
+    if ((s = cuda_check(ctx, cudaStreamSynchronize(st), "rank rule"))) return bail(s);
+    const double eps = p.rank_eps > 0.0 ? p.rank_eps : (double)FLT_EPSILON;
+    const double tol = std::sqrt(std::max(lam[0], 0.0)) * (double)std::max<int64_t>(n, m) * eps;
+    k = 0;
+    while (k < kmax && std::sqrt(std::max(lam[k], 0.0)) > tol) ++k;
+    if (k < 1) k = 1;
+    p.k = k;
+    B = basis_alloc(ctx, m, k, &s);
+    if (!B) return bail(s);
+    if ((s = cuda_check(ctx, cudaMemcpyAsync(B->f, f_dev, (size_t)m * 8, cudaMemcpyDeviceToDevice, st), "f")) ||
+        (s = cuda_check(ctx, cudaMemcpyAsync(B->lam, lam_a, (size_t)k * 8, cudaMemcpyDeviceToDevice, st), "lambda")) ||
+        (s = cuda_check(ctx, cudaMemcpy2DAsync(B->v, (size_t)k * 8, v_a, (size_t)kmax * 8, (size_t)k * 8, m,
+                                               cudaMemcpyDeviceToDevice, st), "V")))
+      return bail(s);
+  } else {
+    if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
+  }
+  B->params = p;
+  B->L = L;
+  FKK_COUNT_LAUNCH(); copy_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_ref, m, B->i_ref);
+  FKK_COUNT_LAUNCH(); trace_kernel<<<1, 256, 0, st>>>(G, m, B->energy);
   FKK_COUNT_LAUNCH(); s_and_w_kernel<<<k, 256, 0, st>>>(B->lam, B->v, m, k, p.ml_lambda, B->s, B->w);
   float* P = (float*)workspace(ctx, "fit_p", (size_t)n * k * 4, &s);
   if (!P) return bail(s);
@@ -257,6 +365,33 @@ fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int6
   return launch_reconstruct(ctx, P, n, B->k, B->m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st);
 }
 
+fkk_status fkk_residual(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int64_t n, int64_t ld,
+                        double* frac_out, void* stream) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!B || !frac_out || !i_cars || n < 1 || ld < B->m) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_residual: bad arguments");
+  if (B->device != ctx->device) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_residual: basis on another device");
+  FKK_TRY(bind(ctx));
+  cudaStream_t st = as_stream(stream);
+  fkk_status s;
+  float* P = (float*)workspace(ctx, "resid_p", (size_t)n * B->k * 4, &s);
+  if (!P) return s;
+  double* acc = (double*)workspace(ctx, "resid_acc", 16, &s);
+  if (!acc) return s;
+  FKK_CUDA(ctx, cudaMemsetAsync(acc, 0, 16, st));
+  // P = A V (the orthonormal V, not the apply's shrunk W)
+  FKK_TRY(launch_project_raw(ctx, i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, B->v, B->f, B->k, P, st));
+  const int grid = (int)std::min<int64_t>((n + 7) / 8, (int64_t)ctx->sm_count * 8);
+  FKK_COUNT_LAUNCH();
+  residual_energy_kernel<<<grid, 256, 0, st>>>(i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, B->f, P, B->k, acc);
+  FKK_CUDA(ctx, cudaGetLastError());
+  double h[2];
+  FKK_CUDA(ctx, cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, st));
+  FKK_CUDA(ctx, cudaStreamSynchronize(st));
+  *frac_out = h[0] > 0.0 ? 1.0 - h[1] / h[0] : 0.0;
+  return FKK_OK;
+}
+
 size_t fkk_fit_params_size(void) { return sizeof(fkk_fit_params); }
 
 fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* params, const double* f,
@@ -266,6 +401,7 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   if (!params || !f || !sv || !v || !c_amp || !c_ph || !i_ref || !out || m < 8 || m > 2048)
     return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_from_arrays: bad arguments");
+  if (params->k < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_from_arrays: k must be >= 1");
   FKK_TRY(check_params(ctx, *params, m, params->k));
   FKK_TRY(bind(ctx));
   const int k = params->k;
@@ -299,6 +435,8 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
   cp(B->c_ph, c_ph, mk * 8);
   cp(B->i_ref, ir.data(), m * 4);
   cp(B->nq, &zero, sizeof zero);
+  const double no_energy = 0.0;  // unknown for an imported basis
+  cp(B->energy, &no_energy, sizeof no_energy);
   if (e == cudaSuccess) e = cudaMemset(B->b, 0, 5 * mk * 8);  // b .. v_sec_t are not part of an imported basis
   if (e != cudaSuccess) {
     s = cuda_check(ctx, e, "fkk_basis_from_arrays");
@@ -442,6 +580,7 @@ fkk_status fkk_basis_get(const fkk_basis* b, int32_t which, double* dst, size_t 
     case FKK_ART_C_AMP: src = b->c_amp; want = mk; break;
     case FKK_ART_C_PH: src = b->c_ph; want = mk; break;
     case FKK_ART_Q: break;
+    case FKK_ART_ENERGY: src = b->energy; want = 1; break;
     default: return FKK_ERR_INVALID_ARG;
   }
   if (cudaSetDevice(b->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FKK_ERR_CUDA;
@@ -506,6 +645,7 @@ fkk_status fkk_basis_math(fkk_ctx* ctx, int32_t m, int32_t k, const double* v, c
   if (!params || !v || !c_amp || !c_ph || m < 8 || m > 2048) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_math: bad arguments");
   fkk_fit_params p = *params;
   p.k = k;
+  if (k < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_math: k must be >= 1");
   FKK_TRY(check_params(ctx, p, m, k));
   if (p.pec && (!x_rows || nq < 1 || nq > 2 * k)) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_basis_math: bad x_rows / nq");
   FKK_TRY(bind(ctx));

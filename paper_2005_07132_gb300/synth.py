@@ -259,3 +259,88 @@ def tile_stream(scene: Scene, sizes, first_image: int = 1):
     1-pixel-high strip with fresh concentrations and noise."""
     for i, n in enumerate(sizes):
         yield make_cube(scene.spec, image=first_image + i, height=1, width=int(n), scene=scene)
+
+
+# ---------------------------------------------------------------------------
+# The simulation-shaped workload of Sec. 4.1 (shape only: the paper's random
+# draws are not published)
+# ---------------------------------------------------------------------------
+
+SIM_BASE = (74, 246)            # base image, 18,204 spectra
+SIM_SIDE_SCALES = (0.5, 1, 2, 3, 4)
+SIM_PEAKS = (22, 25, 10)        # Lorentzian peaks of chemicals 1, 2, 3
+
+
+@dataclass
+class SimCube:
+    i_cars: np.ndarray   # (N, M) float32, noiseless
+    i_ref: np.ndarray    # (M,) float32
+    omega: np.ndarray    # (M,) cm^-1
+    conc: np.ndarray     # (N, 3) concentrations, each row summing to 1
+    chi_r: np.ndarray    # (3, M) complex resonant susceptibility of each chemical
+    chi_nr: np.ndarray   # (3, M) real non-resonant susceptibility of each chemical
+
+    def truth_im(self, rows=None) -> np.ndarray:
+        """Im{chi / chi_nr} of the mixture: the ideal K_CARS's imaginary part."""
+        c = self.conc if rows is None else self.conc[rows]
+        chi = c @ (self.chi_r + self.chi_nr)
+        return (chi / (c @ self.chi_nr)).imag
+
+
+def make_sim_cube(side_scale: float = 1.0, seed: int = 2005, n_channels: int = 810) -> SimCube:
+    """A noiseless three-chemical mixture shaped like the simulation of
+    Sec. 4.1: 810 channels over -500..2,500 cm^-1; chemicals with 22, 25 and
+    10 complex Lorentzian peaks (centre U(500, 1700) cm^-1, width U(5, 20),
+    amplitude U(0.02, 0.3) x width); each chemical's chi_nr a quadratic
+    polynomial in the normalised frequency with non-negative random
+    coefficients; chi_ref a linear polynomial with non-negative
+    coefficients; I_CARS = |sum_s c_s (chi_R,s + chi_nr,s)|^2 and
+    I_ref = chi_ref^2 (constant stimulation profile).  Concentrations: three
+    smooth random maps on the 74 x 246 base image, normalised to sum to 1 at
+    every pixel (a ternary mixture), then side-scaled by `side_scale` with
+    bilinear resampling -- 0.5, 1, 2, 3, 4 give 4,551, 18,204, 72,816,
+    163,836 and 291,264 spectra."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7]))
+    M = n_channels
+    omega = np.linspace(-500.0, 2500.0, M)
+    u = (omega - omega[0]) / (omega[-1] - omega[0])
+    chi_r = np.zeros((3, M), complex)
+    for s, npk in enumerate(SIM_PEAKS):
+        om = rng.uniform(500.0, 1700.0, npk)
+        g = rng.uniform(5.0, 20.0, npk)
+        a = rng.uniform(0.02, 0.3, npk) * g
+        chi_r[s] = (a[:, None] / (om[:, None] - omega[None, :] - 1j * g[:, None])).sum(0)
+    coef = rng.uniform(0.2, 1.0, (3, 3))  # c0 + c1 u + c2 u^2, non-negative
+    chi_nr = coef[:, :1] + coef[:, 1:2] * u[None, :] + coef[:, 2:3] * u[None, :] ** 2
+    d = rng.uniform(0.3, 1.0, 2)
+    chi_ref = d[0] + d[1] * u
+    # ternary concentration maps on the base image
+    h0, w0 = SIM_BASE
+    ky = np.fft.fftfreq(h0)[:, None]
+    kx = np.fft.fftfreq(w0)[None, :]
+    kern = np.exp(-2.0 * np.pi**2 * 6.0**2 * (kx**2 + ky**2))
+    maps = np.stack([np.fft.ifft2(np.fft.fft2(rng.uniform(size=(h0, w0))) * kern).real for _ in range(3)])
+    maps = maps - maps.min(axis=(1, 2), keepdims=True) + 0.05
+    maps = maps / maps.sum(0, keepdims=True)
+    h, w = int(round(h0 * side_scale)), int(round(w0 * side_scale))
+    conc = np.stack([_bilinear(mp, h, w) for mp in maps], axis=-1).reshape(h * w, 3)
+    conc = conc / conc.sum(1, keepdims=True)
+    chi = conc @ (chi_r + chi_nr)
+    i_cars = (np.abs(chi) ** 2).astype(np.float32)
+    return SimCube(i_cars, (chi_ref**2).astype(np.float32), omega, conc, chi_r, chi_nr)
+
+
+def _bilinear(img: np.ndarray, h: int, w: int) -> np.ndarray:
+    """Resample img to h x w, pixel centres aligned (edge-clamped)."""
+    h0, w0 = img.shape
+    y = np.clip((np.arange(h) + 0.5) * h0 / h - 0.5, 0.0, h0 - 1.0)
+    x = np.clip((np.arange(w) + 0.5) * w0 / w - 0.5, 0.0, w0 - 1.0)
+    y0 = np.floor(y).astype(int)
+    x0 = np.floor(x).astype(int)
+    y1 = np.minimum(y0 + 1, h0 - 1)
+    x1 = np.minimum(x0 + 1, w0 - 1)
+    fy = (y - y0)[:, None]
+    fx = (x - x0)[None, :]
+    top = img[y0][:, x0] * (1 - fx) + img[y0][:, x1] * fx
+    bot = img[y1][:, x0] * (1 - fx) + img[y1][:, x1] * fx
+    return top * (1 - fy) + bot * fy

@@ -292,7 +292,7 @@ def test_apply_on_training_equals_fit(fk, ctx, cube1):
 def test_fit_errors(fk, ctx, cube1):
     x = _dev(cube1.i_cars)
     ref = _dev(cube1.i_ref)
-    for bad in (dict(k=0), dict(k=81), dict(als_p=1.5), dict(ratio_floor=0.0), dict(sg_window=4),
+    for bad in (dict(k=0, k_max=0), dict(k=81), dict(als_p=1.5), dict(ratio_floor=0.0), dict(sg_window=4),
                 dict(pad_len=100)):
         with pytest.raises(fk.FkkError):
             fk.fkk_fit_basis(ctx, x, ref, fk.fit_params(**bad))

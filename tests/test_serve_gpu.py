@@ -56,7 +56,7 @@ def test_basis_save_load_roundtrip(fk, ctx, trained, tmp_path):
     basis.save(path)
     b2 = fk.fkk_basis_load(ctx, path)
     assert b2.info() == basis.info()
-    for art in ("s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q"):
+    for art in ("s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q", "energy"):
         np.testing.assert_array_equal(b2.get(art), basis.get(art))
     a1 = _reference(fk, ctx, basis, x)
     a2 = _reference(fk, ctx, b2, x)
