@@ -64,6 +64,10 @@ class FitParams:
     ratio_floor: float = 1e-6
     k_max: int = 80          # k = 0: the rank rule picks k <= k_max
     rank_eps: float = 0.0    # epsilon of the rank rule; 0 -> float32 machine epsilon
+    svd: str = "exact"       # "exact" (eigenpairs of A^T A) or "randomized" (Sec. 5: Halko et al.)
+    rsvd_oversample: int = 10
+    rsvd_power_iters: int = 2
+    rsvd_seed: int = 0
 
 
 def pad_len(n_channels: int) -> int:
@@ -233,6 +237,80 @@ def residual_fraction(basis: "Basis", i_new) -> float:
     A = log_ratio(i_new, basis.i_ref, basis.f, basis.params.ratio_floor)
     PV = A @ basis.V
     return float(1.0 - np.sum(PV * PV) / np.sum(A * A))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5 (the randomised SVD the paper proposes, Halko, Martinsson & Tropp
+# 2011): counter-based random numbers and randomised subspace iteration
+# ---------------------------------------------------------------------------
+
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)  # Philox4x64 multipliers
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)  # key increments (Weyl)
+_U64 = (1 << 64) - 1
+
+
+def philox4x64(ctr, key, rounds: int = 10):
+    """Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): 4 x 64-bit counter,
+    2 x 64-bit key; each round multiplies words 0 and 2 by the constants,
+    mixes the high halves with words 1, 3 and the key, then bumps the key."""
+    x0, x1, x2, x3 = (int(v) & _U64 for v in ctr)
+    k0, k1 = (int(v) & _U64 for v in key)
+    for _ in range(rounds):
+        p0 = _PHILOX_M[0] * x0
+        p1 = _PHILOX_M[1] * x2
+        x0, x1, x2, x3 = ((p1 >> 64) ^ x1 ^ k0) & _U64, p1 & _U64, ((p0 >> 64) ^ x3 ^ k1) & _U64, p0 & _U64
+        k0 = (k0 + _PHILOX_W[0]) & _U64
+        k1 = (k1 + _PHILOX_W[1]) & _U64
+    return x0, x1, x2, x3
+
+
+def philox_normals(count: int, seed: int) -> np.ndarray:
+    """count standard normals: entry e comes from Philox4x64-10 at counter
+    (e // 2, 0, 0, 0) with key (seed, 0); its first two words give uniforms
+    u = (w >> 11 + 1/2) 2^-53 in (0, 1), and Box-Muller gives
+    sqrt(-2 ln u1) cos(2 pi u2) (even e) or sin(2 pi u2) (odd e)."""
+    out = np.empty(count)
+    for b in range((count + 1) // 2):
+        w0, w1, _, _ = philox4x64((b, 0, 0, 0), (seed, 0))
+        u1 = ((w0 >> 11) + 0.5) * 2.0**-53
+        u2 = ((w1 >> 11) + 0.5) * 2.0**-53
+        r = np.sqrt(-2.0 * np.log(u1))
+        out[2 * b] = r * np.cos(2.0 * np.pi * u2)
+        if 2 * b + 1 < count:
+            out[2 * b + 1] = r * np.sin(2.0 * np.pi * u2)
+    return out
+
+
+def _orth(Y) -> np.ndarray:
+    """An orthonormal basis of the range of Y (Householder QR)."""
+    return np.linalg.qr(Y)[0]
+
+
+def rsvd(matvec, rmatvec, n: int, m: int, k: int, oversample: int, power_iters: int, seed: int):
+    """Randomised SVD of an n x m matrix A given A X (matvec) and A^T Y
+    (rmatvec): randomised subspace iteration (Halko et al. 2011, Alg. 4.4)
+    with l = k + oversample Gaussian test vectors, then the SVD of the small
+    B = Q^T A through the eigenpairs of B B^T.  Returns (lambda, V) for the k
+    largest: lambda = s^2, V (m x k) with its largest-magnitude component
+    positive in each column."""
+    l = min(k + oversample, m)
+    Om = philox_normals(m * l, seed).reshape(m, l)
+    Y = matvec(Om)
+    for _ in range(power_iters):
+        Q = _orth(Y)
+        Z = _orth(rmatvec(Q))
+        Y = matvec(Z)
+    Q = _orth(Y)
+    B = rmatvec(Q).T  # l x m
+    lam, U = np.linalg.eigh(B @ B.T)
+    order = np.argsort(lam)[::-1][:k]
+    lam, U = lam[order], U[:, order]
+    s = np.sqrt(np.maximum(lam, 0.0))
+    V = (B.T @ U) / np.where(s > 0, s, 1.0)
+    idx = np.argmax(np.abs(V), axis=0)
+    sign = np.sign(V[idx, np.arange(k)])
+    sign[sign == 0] = 1.0
+    return lam, V * sign
 
 
 def singular_from_eig(lam) -> np.ndarray:
@@ -416,13 +494,37 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
     N, M = i_cars.shape
     L = params.pad_len or pad_len(M)
     f = np.ones(M) if f is None else np.asarray(f, F64)
+    def blocks():
+        for a in range(0, N, chunk):
+            yield a, log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor)
+
     G = np.zeros((M, M))
-    for a in range(0, N, chunk):
-        A = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor)
+    for _, A in blocks():
         G += A.T @ A
-    lam, Vall = eig_desc(G)
-    k = params.k or rank_k(lam, N, M, params.k_max, params.rank_eps)
-    V = Vall[:, :k]
+    if params.svd == "randomized":
+        if not params.k:
+            raise ValueError("the randomised SVD needs a fixed k")
+        k = params.k
+
+        def matvec(X):
+            out = np.empty((N, X.shape[1]))
+            for a, A in blocks():
+                out[a : a + A.shape[0]] = A @ X
+            return out
+
+        def rmatvec(Y):
+            out = np.zeros((M, Y.shape[1]))
+            for a, A in blocks():
+                out += A.T @ Y[a : a + A.shape[0]]
+            return out
+
+        lam, V = rsvd(matvec, rmatvec, N, M, k, params.rsvd_oversample, params.rsvd_power_iters, params.rsvd_seed)
+    elif params.svd == "exact":
+        lam, Vall = eig_desc(G)
+        k = params.k or rank_k(lam, N, M, params.k_max, params.rank_eps)
+        V = Vall[:, :k]
+    else:
+        raise ValueError(params.svd)
     s = singular_from_eig(lam[:k])
     P = np.empty((N, k))
     for a in range(0, N, chunk):
