@@ -158,12 +158,37 @@ typedef struct {
   double noise_sigma_g; /* Gaussian sigma_g of f(w); alpha = sigma_g = 0 means f = 1 */
   int32_t k_max;        /* k = 0: upper bound of the chosen k, 1..80 */
   double rank_eps;      /* k = 0: the epsilon of the rank rule (> 0); 0 = FLT_EPSILON, the input's */
+  int32_t svd;          /* FKK_SVD_EXACT or FKK_SVD_RANDOMIZED (the right singular vectors' source) */
+  int32_t rsvd_oversample;   /* randomised: l = k + oversample test vectors (l <= 80) */
+  int32_t rsvd_power_iters;  /* randomised: subspace iterations, 0..20 */
+  uint64_t rsvd_seed;        /* randomised: key of the Philox4x64-10 test matrix */
 } fkk_fit_params;
+
+/* How fkk_fit_basis finds V_k and s:
+ *   FKK_SVD_EXACT      the k largest eigenpairs of A^T A (tensor-core Gram,
+ *                      double-word tridiagonal eigensolver);
+ *   FKK_SVD_RANDOMIZED randomised subspace iteration (the randomised SVD
+ *                      Sec. 5 proposes; Halko, Martinsson & Tropp 2011):
+ *                      Omega (M x l) Gaussian, entry e from Philox4x64-10 at
+ *                      counter (e/2, 0, 0, 0), key (rsvd_seed, 0), Box-Muller
+ *                      cos/sin of u = ((w >> 11) + 1/2) 2^-53 of words 0, 1;
+ *                      Y = A Omega; rsvd_power_iters times Q = orth(Y),
+ *                      Z = orth(A^T Q), Y = A Z; Q = orth(Y); B = Q^T A;
+ *                      V = B^T U S^-1 from B B^T = U S^2 U^T.  It reads the
+ *                      cube 2 (power_iters + 1) times instead of forming
+ *                      A^T A, and needs k >= 1. */
+enum { FKK_SVD_EXACT = 0, FKK_SVD_RANDOMIZED = 1 };
+
+/* The randomised SVD's test-matrix entries 0..count-1 for `seed` (as
+ * described above), written as doubles to the device array out.
+ * Asynchronous on `stream`. */
+fkk_status fkk_philox_normals(fkk_ctx* ctx, int64_t count, uint64_t seed, double* out, void* stream);
 
 /* Defaults: k 20, pad_len 0, pec 1, sec 1, als_lambda 0 (auto), als_p 0.01,
  * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
  * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
- * k_max 80, rank_eps 0 (FLT_EPSILON).
+ * k_max 80, rank_eps 0 (FLT_EPSILON), svd EXACT, rsvd_oversample 10,
+ * rsvd_power_iters 2, rsvd_seed 0.
  *
  * k = 0 selects the number of basis vectors by the rank rule of Sec. 4.1:
  * the count of singular values s_i > s_1 * max(N, M) * rank_eps (the NumPy /

@@ -498,9 +498,7 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
         for a in range(0, N, chunk):
             yield a, log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor)
 
-    G = np.zeros((M, M))
-    for _, A in blocks():
-        G += A.T @ A
+    G = None
     if params.svd == "randomized":
         if not params.k:
             raise ValueError("the randomised SVD needs a fixed k")
@@ -520,6 +518,9 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
 
         lam, V = rsvd(matvec, rmatvec, N, M, k, params.rsvd_oversample, params.rsvd_power_iters, params.rsvd_seed)
     elif params.svd == "exact":
+        G = np.zeros((M, M))
+        for _, A in blocks():
+            G += A.T @ A
         lam, Vall = eig_desc(G)
         k = params.k or rank_k(lam, N, M, params.k_max, params.rank_eps)
         V = Vall[:, :k]
@@ -531,7 +532,8 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
         P[a : a + chunk] = log_ratio(i_cars[a : a + chunk], i_ref, f, params.ratio_floor) @ V
     B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph, q = basis_math(V, P, f, params, L)
     basis = Basis(f, s, V, B, H_B, phi_pec_t, H_phi, v_sec_t, c_amp, c_ph,
-                  np.asarray(i_ref, F64), params, {"lam": lam, "q": q, "G": G, "k": k, "energy": float(np.trace(G))})
+                  np.asarray(i_ref, F64), params, {"lam": lam, "q": q, "G": G, "k": k,
+                   "energy": float(np.trace(G)) if G is not None else float(sum(np.sum(A * A) for _, A in blocks()))})
     rows = slice(None) if out_rows is None else out_rows
     re, im = reconstruct(P[rows], c_amp, c_ph)
     return basis, P, {"re": re, "im": im, "lam": lam, "q": q, "k": k}

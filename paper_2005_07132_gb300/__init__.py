@@ -10,6 +10,8 @@ if the library has not been built.
 from ._lib import (  # noqa: F401
     SEC_MEAN,
     SEC_SAVGOL,
+    SVD_EXACT,
+    SVD_RANDOMIZED,
     Basis,
     Context,
     FitParams,
@@ -29,14 +31,15 @@ from ._lib import (  # noqa: F401
     kk_per_spectrum,
     conventional_per_spectrum,
     fkk_residual,
+    fkk_philox_normals,
     launch_count,
     lib,
     Server,
 )
 
 __all__ = [
-    "Basis", "Context", "FitParams", "FkkError", "SEC_MEAN", "SEC_SAVGOL", "fit_params", "fkk_apply",
+    "Basis", "Context", "FitParams", "FkkError", "SEC_MEAN", "SEC_SAVGOL", "SVD_EXACT", "SVD_RANDOMIZED", "fit_params", "fkk_apply",
     "fkk_basis_from_arrays", "fkk_basis_load", "fkk_noise_scale", "Server", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_gram", "fkk_project",
-    "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "conventional_per_spectrum", "fkk_residual",
+    "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "conventional_per_spectrum", "fkk_residual", "fkk_philox_normals",
     "launch_count", "lib",
 ]

@@ -54,6 +54,7 @@ SIGNATURES = {
     "kk_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _I32, _F32, _P, _P, _I64, _P]),
     "conventional_per_spectrum": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, _P, _I64, _P]),
     "fkk_residual": (_I32, [_P, _P, _P, _I64, _I64, C.POINTER(C.c_double), _P]),
+    "fkk_philox_normals": (_I32, [_P, _I64, C.c_uint64, _P, _P]),
     "fkk_fit_params_default": (None, [_P]),
     "fkk_fit_params_size": (_SZ, []),
     "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
@@ -89,10 +90,13 @@ class FitParams(C.Structure):
         ("sg_order", C.c_int32), ("ml_lambda", C.c_double), ("precision", C.c_int32),
         ("ratio_floor", C.c_float), ("noise_alpha", C.c_double), ("noise_sigma_g", C.c_double),
         ("k_max", C.c_int32), ("rank_eps", C.c_double),
+        ("svd", C.c_int32), ("rsvd_oversample", C.c_int32), ("rsvd_power_iters", C.c_int32),
+        ("rsvd_seed", C.c_uint64),
     ]
 
 
 SEC_SAVGOL, SEC_MEAN = 0, 1
+SVD_EXACT, SVD_RANDOMIZED = 0, 1
 ART = {name: i for i, name in enumerate(
     ["s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q", "energy"])}
 
@@ -262,6 +266,15 @@ def conventional_per_spectrum(ctx: Context, i_cars, i_ref, params: "FitParams", 
                                          _stream(stream))
     ctx.check(st, "conventional_per_spectrum")
     return (im_out, re_out) if re_out is not None else im_out
+
+
+def fkk_philox_normals(ctx: Context, count: int, seed: int, stream=None):
+    """The randomised SVD's test-matrix entries (fkk_philox_normals)."""
+    import torch
+
+    out = torch.empty(count, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.check(lib().fkk_philox_normals(ctx.handle, count, seed, _ptr(out), _stream(stream)), "fkk_philox_normals")
+    return out
 
 
 def fkk_residual(ctx: Context, basis: "Basis", i_cars, stream=None) -> float:

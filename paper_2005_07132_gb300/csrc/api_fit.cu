@@ -56,6 +56,27 @@ __global__ void copy_f32_kernel(const float* __restrict__ a, int m, float* __res
   if (j < m) b[j] = a[j];
 }
 
+// *out = ||A||_F^2 = sum_j f_j^2 (sum_n d^2 + 2 c_j sum_n d + n c_j^2) (d the
+// shifted log ratio, a = d + c), one block.
+__global__ void energy_kernel(const double* __restrict__ sd2, const double* __restrict__ sd,
+                              const float* __restrict__ c, const double* __restrict__ f, int64_t n, int m,
+                              double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double cj = c[j];
+    t += f[j] * f[j] * (sd2[j] + 2.0 * cj * sd[j] + (double)n * cj * cj);
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+    *out = u;
+  }
+}
+
 // *out = trace(G), one block.
 __global__ void trace_kernel(const double* __restrict__ g, int m, double* __restrict__ out) {
   __shared__ double red[32];
@@ -136,6 +157,14 @@ fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n)
   if (!(p.ratio_floor > 0.f)) return fail(ctx, FKK_ERR_INVALID_ARG, "ratio_floor must be > 0");
   if (p.precision != FKK_PREC_BF16X3) return fail(ctx, FKK_ERR_INVALID_ARG, "unknown precision");
   if (p.noise_alpha < 0.0 || p.noise_sigma_g < 0.0) return fail(ctx, FKK_ERR_INVALID_ARG, "negative noise parameter");
+  if (p.svd != FKK_SVD_EXACT && p.svd != FKK_SVD_RANDOMIZED) return fail(ctx, FKK_ERR_INVALID_ARG, "bad svd");
+  if (p.svd == FKK_SVD_RANDOMIZED) {
+    if (p.k < 1) return fail(ctx, FKK_ERR_INVALID_ARG, "the randomised SVD needs k >= 1");
+    if (p.rsvd_oversample < 0 || p.k + p.rsvd_oversample > 80)
+      return fail(ctx, FKK_ERR_INVALID_ARG, "randomised SVD: k + oversample = %d must be <= 80", p.k + p.rsvd_oversample);
+    if (p.rsvd_power_iters < 0 || p.rsvd_power_iters > 20)
+      return fail(ctx, FKK_ERR_INVALID_ARG, "randomised SVD: power_iters %d not in 0..20", p.rsvd_power_iters);
+  }
   return FKK_OK;
 }
 
@@ -235,6 +264,10 @@ void fkk_fit_params_default(fkk_fit_params* p) {
   p->noise_sigma_g = 0.0;
   p->k_max = 80;
   p->rank_eps = 0.0;
+  p->svd = FKK_SVD_EXACT;
+  p->rsvd_oversample = 10;
+  p->rsvd_power_iters = 2;
+  p->rsvd_seed = 0;
 }
 
 fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,
@@ -284,43 +317,54 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   } else {
     FKK_COUNT_LAUNCH(); f_from_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(nullptr, m, f_dev);
   }
-  double* G = (double*)workspace(ctx, "fit_gram", (size_t)m * m * 8, &s);
-  if (!G) return bail(s);
+  double* G = nullptr;
   stage_mark(ctx, 1, st);
-  if ((s = launch_gram(ctx, D, f_dev, G, st))) return bail(s);
-  stage_mark(ctx, 2, st);
-  if (autok) {
-    // the k_max largest eigenpairs, then the rank rule on the host
-    const int kmax = std::min(p.k_max, m);
-    double* lam_a = (double*)workspace(ctx, "fit_lam_auto", (size_t)kmax * 8, &s);
-    if (!lam_a) return bail(s);
-    double* v_a = (double*)workspace(ctx, "fit_v_auto", (size_t)m * kmax * 8, &s);
-    if (!v_a) return bail(s);
-    if ((s = launch_eig_topk(ctx, G, m, kmax, lam_a, v_a, st))) return bail(s);
-    std::vector<double> lam(kmax);
-    if ((s = cuda_check(ctx, cudaMemcpyAsync(lam.data(), lam_a, kmax * 8, cudaMemcpyDeviceToHost, st), "lambda")))
-      return bail(s);
-    if ((s = cuda_check(ctx, cudaStreamSynchronize(st), "rank rule"))) return bail(s);
-    const double eps = p.rank_eps > 0.0 ? p.rank_eps : (double)FLT_EPSILON;
-    const double tol = std::sqrt(std::max(lam[0], 0.0)) * (double)std::max<int64_t>(n, m) * eps;
-    k = 0;
-    while (k < kmax && std::sqrt(std::max(lam[k], 0.0)) > tol) ++k;
-    if (k < 1) k = 1;
-    p.k = k;
-    B = basis_alloc(ctx, m, k, &s);
-    if (!B) return bail(s);
-    if ((s = cuda_check(ctx, cudaMemcpyAsync(B->f, f_dev, (size_t)m * 8, cudaMemcpyDeviceToDevice, st), "f")) ||
-        (s = cuda_check(ctx, cudaMemcpyAsync(B->lam, lam_a, (size_t)k * 8, cudaMemcpyDeviceToDevice, st), "lambda")) ||
-        (s = cuda_check(ctx, cudaMemcpy2DAsync(B->v, (size_t)k * 8, v_a, (size_t)kmax * 8, (size_t)k * 8, m,
-                                               cudaMemcpyDeviceToDevice, st), "V")))
+  if (p.svd == FKK_SVD_RANDOMIZED) {  // k fixed: B was allocated above, f_dev is B->f
+    stage_mark(ctx, 2, st);
+    if ((s = launch_rsvd(ctx, D, B->f, k, p.rsvd_oversample, p.rsvd_power_iters, p.rsvd_seed, B->lam, B->v, st)))
       return bail(s);
   } else {
-    if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
+    G = (double*)workspace(ctx, "fit_gram", (size_t)m * m * 8, &s);
+    if (!G) return bail(s);
+    if ((s = launch_gram(ctx, D, f_dev, G, st))) return bail(s);
+    stage_mark(ctx, 2, st);
+    if (autok) {
+      // the k_max largest eigenpairs, then the rank rule on the host
+      const int kmax = std::min(p.k_max, m);
+      double* lam_a = (double*)workspace(ctx, "fit_lam_auto", (size_t)kmax * 8, &s);
+      if (!lam_a) return bail(s);
+      double* v_a = (double*)workspace(ctx, "fit_v_auto", (size_t)m * kmax * 8, &s);
+      if (!v_a) return bail(s);
+      if ((s = launch_eig_topk(ctx, G, m, kmax, lam_a, v_a, st))) return bail(s);
+      std::vector<double> lam(kmax);
+      if ((s = cuda_check(ctx, cudaMemcpyAsync(lam.data(), lam_a, kmax * 8, cudaMemcpyDeviceToHost, st), "lambda")))
+        return bail(s);
+      if ((s = cuda_check(ctx, cudaStreamSynchronize(st), "rank rule"))) return bail(s);
+      const double eps = p.rank_eps > 0.0 ? p.rank_eps : (double)FLT_EPSILON;
+      const double tol = std::sqrt(std::max(lam[0], 0.0)) * (double)std::max<int64_t>(n, m) * eps;
+      k = 0;
+      while (k < kmax && std::sqrt(std::max(lam[k], 0.0)) > tol) ++k;
+      if (k < 1) k = 1;
+      p.k = k;
+      B = basis_alloc(ctx, m, k, &s);
+      if (!B) return bail(s);
+      if ((s = cuda_check(ctx, cudaMemcpyAsync(B->f, f_dev, (size_t)m * 8, cudaMemcpyDeviceToDevice, st), "f")) ||
+          (s = cuda_check(ctx, cudaMemcpyAsync(B->lam, lam_a, (size_t)k * 8, cudaMemcpyDeviceToDevice, st), "lambda")) ||
+          (s = cuda_check(ctx, cudaMemcpy2DAsync(B->v, (size_t)k * 8, v_a, (size_t)kmax * 8, (size_t)k * 8, m,
+                                                 cudaMemcpyDeviceToDevice, st), "V")))
+        return bail(s);
+    } else {
+      if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
+    }
   }
   B->params = p;
   B->L = L;
   FKK_COUNT_LAUNCH(); copy_f32_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_ref, m, B->i_ref);
-  FKK_COUNT_LAUNCH(); trace_kernel<<<1, 256, 0, st>>>(G, m, B->energy);
+  if (G) {
+    FKK_COUNT_LAUNCH(); trace_kernel<<<1, 256, 0, st>>>(G, m, B->energy);
+  } else {
+    FKK_COUNT_LAUNCH(); energy_kernel<<<1, 256, 0, st>>>(D.sum_d2, D.sum_d, D.c, B->f, n, m, B->energy);
+  }
   FKK_COUNT_LAUNCH(); s_and_w_kernel<<<k, 256, 0, st>>>(B->lam, B->v, m, k, p.ml_lambda, B->s, B->w);
   float* P = (float*)workspace(ctx, "fit_p", (size_t)n * k * 4, &s);
   if (!P) return bail(s);

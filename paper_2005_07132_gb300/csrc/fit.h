@@ -18,6 +18,7 @@ struct DtLayout {
   float* c = nullptr;        // per-channel shift (m)
   double* sum_d = nullptr;   // sum_n d[n, j] (m)
   double* sum_i = nullptr;   // sum_n I[n, j] (m)
+  double* sum_d2 = nullptr;  // sum_n d[n, j]^2 (m)
 };
 
 struct TransformArgs {
@@ -33,6 +34,7 @@ struct TransformArgs {
   __nv_bfloat16* dt_lo;
   double* part_d;
   double* part_i;
+  double* part_d2;
   long long* status;
 };
 
@@ -121,6 +123,31 @@ fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n
 fkk_status launch_kk_phase(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
                            const float* i_ref, int L, float floor_, float* phi, int64_t ld_phi,
                            cudaStream_t st);
+
+// Small fp64 Cholesky-QR steps (m x k row-major, k small): W = Z^T Z;
+// R^-1 with W = R^T R -- a pivot below drop_tol of its column's squared norm
+// is FKK_ERR_NOT_CONVERGED when strict, else that column is dropped (its
+// column of Z R^-1 is 0); V = Z R^-1; the largest-magnitude component of each
+// column made positive.
+fkk_status launch_ztz(fkk_ctx* ctx, const double* z, int m, int k, double* w, cudaStream_t st);
+fkk_status launch_chol_inv(fkk_ctx* ctx, const double* w, int k, double* rinv, cudaStream_t st, double drop_tol,
+                           bool strict);
+fkk_status launch_apply_rinv(fkk_ctx* ctx, const double* z, int m, int k, const double* rinv, double* v,
+                             cudaStream_t st);
+fkk_status launch_sign_fix(fkk_ctx* ctx, double* v, int m, int k, cudaStream_t st);
+
+// Z = A^T Q (m x l fp64) for the transformed cube and Q given as Q^T in
+// bf16 hi / lo ([tn][np], tn = 64 or 128 >= l, zero beyond l and n) with its
+// column sums (for the shift c); f may be null (f = 1).
+fkk_status launch_atq(fkk_ctx* ctx, const DtLayout& L, const __nv_bfloat16* qt_hi, const __nv_bfloat16* qt_lo,
+                      int tn, int l, const double* colsum, const double* f, double* z, cudaStream_t st);
+
+// Randomised SVD of A (the transformed cube scaled by f): randomised subspace
+// iteration with l = k + oversample Philox4x64-10 Gaussian test vectors
+// (counter e / 2, key (seed, 0), Box-Muller) and `power_iters` iterations;
+// lam (k) = s^2 and v (m x k) of the k largest, as launch_eig_topk.
+fkk_status launch_rsvd(fkk_ctx* ctx, const DtLayout& L, const double* f, int k, int oversample, int power_iters,
+                       uint64_t seed, double* lam, double* v, cudaStream_t st);
 
 // Tensor map helper (driver entry point fetched once).
 fkk_status make_tmap_2d(fkk_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t inner,

@@ -32,6 +32,7 @@ __global__ void shift_kernel(const float* __restrict__ i_cars, int64_t n, int m,
 __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   __shared__ float tile[64][65];
   __shared__ double red_d[4][64];
+  __shared__ double red_d2[4][64];
   __shared__ double red_i[4][64];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int j0 = blockIdx.y * 64;
@@ -40,11 +41,11 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   const float rinv = jvalid ? 1.f / p.i_ref[j] : 1.f;
   const float cj = jvalid ? p.c[j] : 0.f;
   const int64_t nrt = p.np / 64;
-  double sum_d = 0.0, sum_i = 0.0;
+  double sum_d = 0.0, sum_i = 0.0, sum_d2 = 0.0;
   int clamped = 0;
   for (int64_t rt = blockIdx.x; rt < nrt; rt += gridDim.x) {
     const int64_t n0 = rt * 64;
-    float td = 0.f, ti = 0.f;
+    float td = 0.f, ti = 0.f, td2 = 0.f;
     // all 16 loads of this thread in flight before any arithmetic
     float vals[16];
 #pragma unroll
@@ -63,11 +64,13 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
         if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
         d = 0.5f * logf(x) - cj;
         td += d;
+        td2 = fmaf(d, d, td2);
         ti += v;
       }
       tile[tx][rr] = d;
     }
     sum_d += td;
+    sum_d2 += td2;
     sum_i += ti;
     __syncthreads();
     // transposed write: warp w handles channels w, w+8, ..., 32 lanes x 2 bf16
@@ -84,12 +87,14 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
     __syncthreads();
   }
   red_d[ty][tx] = sum_d;
+  red_d2[ty][tx] = sum_d2;
   red_i[ty][tx] = sum_i;
   __syncthreads();
   if (ty == 0 && jvalid) {
     double sd = red_d[0][tx] + red_d[1][tx] + red_d[2][tx] + red_d[3][tx];
     double si = red_i[0][tx] + red_i[1][tx] + red_i[2][tx] + red_i[3][tx];
     p.part_d[(int64_t)blockIdx.x * p.m + j] = sd;
+    p.part_d2[(int64_t)blockIdx.x * p.m + j] = red_d2[0][tx] + red_d2[1][tx] + red_d2[2][tx] + red_d2[3][tx];
     p.part_i[(int64_t)blockIdx.x * p.m + j] = si;
   }
   for (int o = 16; o > 0; o >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, o);
@@ -98,17 +103,20 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
 }
 
 __global__ void colsum_reduce_kernel(const double* __restrict__ part_d, const double* __restrict__ part_i,
-                                     int nparts, int m, double* __restrict__ sum_d,
-                                     double* __restrict__ sum_i) {
+                                     const double* __restrict__ part_d2, int nparts, int m,
+                                     double* __restrict__ sum_d, double* __restrict__ sum_i,
+                                     double* __restrict__ sum_d2) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  double a = 0.0, b = 0.0;
+  double a = 0.0, b = 0.0, c2 = 0.0;
   for (int t = 0; t < nparts; ++t) {
     a += part_d[(int64_t)t * m + j];
     b += part_i[(int64_t)t * m + j];
+    c2 += part_d2[(int64_t)t * m + j];
   }
   sum_d[j] = a;
   sum_i[j] = b;
+  sum_d2[j] = c2;
 }
 
 }  // namespace
@@ -132,6 +140,8 @@ fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m,
   if (!L.sum_d) return s;
   L.sum_i = (double*)workspace(ctx, "sum_i", (size_t)m * 8, &s);
   if (!L.sum_i) return s;
+  L.sum_d2 = (double*)workspace(ctx, "sum_d2", (size_t)m * 8, &s);
+  if (!L.sum_d2) return s;
   const int ctiles = L.mg / 64;
   const int64_t nrt = L.np / 64;
   int64_t grows = (int64_t)ctx->sm_count * 8 / ctiles;
@@ -141,10 +151,14 @@ fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m,
   if (!part_d) return s;
   double* part_i = (double*)workspace(ctx, "part_i", (size_t)grows * m * 8, &s);
   if (!part_i) return s;
+  double* part_d2 = (double*)workspace(ctx, "part_d2", (size_t)grows * m * 8, &s);
+  if (!part_d2) return s;
   FKK_COUNT_LAUNCH(); shift_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_cars, n, m, ld, i_ref, floor_, L.c);
-  TransformArgs a{i_cars, n, m, ld, i_ref, floor_, L.c, L.np, L.dt_hi, L.dt_lo, part_d, part_i, ctx->d_status};
+  TransformArgs a{i_cars, n, m, ld, i_ref, floor_, L.c, L.np, L.dt_hi, L.dt_lo, part_d, part_i, part_d2, ctx->d_status};
   FKK_COUNT_LAUNCH(); transform_kernel<<<dim3((unsigned)grows, ctiles), 256, 0, st>>>(a);
-  FKK_COUNT_LAUNCH(); colsum_reduce_kernel<<<(m + 127) / 128, 128, 0, st>>>(part_d, part_i, (int)grows, m, L.sum_d, L.sum_i);
+  FKK_COUNT_LAUNCH();
+  colsum_reduce_kernel<<<(m + 127) / 128, 128, 0, st>>>(part_d, part_i, part_d2, (int)grows, m, L.sum_d, L.sum_i,
+                                                        L.sum_d2);
   return cuda_check(ctx, cudaGetLastError(), "transform launch");
 }
 

@@ -58,16 +58,17 @@ constexpr int kBK = 64;                       // spectra per K-block (128 bytes 
 constexpr int kTileM = 128, kTileN = 256;
 constexpr int kStages = 2;
 constexpr uint32_t kABytes = kTileM * kBK * 2;  // 16 KB per term
-constexpr uint32_t kBBytes = kTileN * kBK * 2;  // 32 KB per term
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr size_t kGramSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+template <int TN>
+constexpr uint32_t stage_bytes() { return 2 * kABytes + 2 * (uint32_t)TN * kBK * 2; }
+template <int TN>
+constexpr size_t gram_smem() { return kStages * stage_bytes<TN>() + 1024 /*align*/ + 256 /*barriers*/; }
 
 struct GramArgs {
   int mb;        // row blocks of 128
   int ntiles;
   int64_t nkb;   // K-blocks of 64 spectra
   int splits;
-  float* partial;  // [splits][ntiles][128][256]
+  float* partial;  // [splits][ntiles][128][TN]
   long long* status;
 };
 
@@ -82,10 +83,16 @@ __host__ __device__ inline void gram_tile(int t, int mb, int& ib, int& jb) {
   }
 }
 
+// TN: columns of an output tile (the B operand's rows per K-block).  RECT:
+// the tiles are the mb row blocks of one column block (A^T Q, Q with at most
+// TN columns) instead of the upper triangle of A^T A.
+template <int TN, bool RECT>
 __global__ void __launch_bounds__(128, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tm_a_hi, const __grid_constant__ CUtensorMap tm_a_lo,
                    const __grid_constant__ CUtensorMap tm_b_hi, const __grid_constant__ CUtensorMap tm_b_lo,
                    GramArgs p) {
+  constexpr uint32_t kBBytes = (uint32_t)TN * kBK * 2;
+  constexpr uint32_t kStageBytes = stage_bytes<TN>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -96,7 +103,12 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int ib, jb;
-  gram_tile(blockIdx.x, p.mb, ib, jb);
+  if (RECT) {
+    ib = blockIdx.x;
+    jb = 0;
+  } else {
+    gram_tile(blockIdx.x, p.mb, ib, jb);
+  }
   const int split = blockIdx.y;
   const int64_t kb0 = p.nkb * split / p.splits;
   const int64_t kb1 = p.nkb * (split + 1) / p.splits;
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(128, 1)
     tc::prefetch_tmap(&tm_b_hi);
     tc::prefetch_tmap(&tm_b_lo);
   }
-  if (warp == 2) tc::tmem_alloc(tmem_slot, 256);
+  if (warp == 2) tc::tmem_alloc(tmem_slot, TN);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -132,12 +144,12 @@ __global__ void __launch_bounds__(128, 1)
       const int x = (int)((kb0 + i) * kBK);
       tc::tma_load_2d(st, &tm_a_hi, &full[s], x, ib * kTileM);
       tc::tma_load_2d(st + kABytes, &tm_a_lo, &full[s], x, ib * kTileM);
-      tc::tma_load_2d(st + 2 * kABytes, &tm_b_hi, &full[s], x, jb * kTileN);
-      tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tm_b_lo, &full[s], x, jb * kTileN);
+      tc::tma_load_2d(st + 2 * kABytes, &tm_b_hi, &full[s], x, jb * TN);
+      tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tm_b_lo, &full[s], x, jb * TN);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, TN);
     bool ok = true;
     for (int i = 0; i < nk; ++i) {
       const int s = i % kStages;
@@ -173,9 +185,9 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc::tc_fence_after();
   const int row = warp * 32 + lane;
-  float* out = p.partial + (((int64_t)split * p.ntiles + blockIdx.x) * kTileM + row) * kTileN;
+  float* out = p.partial + (((int64_t)split * p.ntiles + blockIdx.x) * kTileM + row) * TN;
   const bool failed = fail_s != 0;
-  for (int c = 0; c < kTileN / 32; ++c) {
+  for (int c = 0; c < TN / 32; ++c) {
     float v[32];
     if (have && !failed) {
       tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + c * 32, v);
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(128, 1)
   if (failed && threadIdx.x == 0) record_error(p.status, kErrTimeout);
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 2) tc::tmem_dealloc(taddr, 256);
+  if (warp == 2) tc::tmem_dealloc(taddr, TN);
 }
 
 // Sum partial tiles (fixed split order, fp64), add the shift terms, scale by
@@ -232,6 +244,62 @@ fkk_status launch_noise_scale(fkk_ctx* ctx, const double* sum_i, int64_t n, int 
   return cuda_check(ctx, cudaGetLastError(), "noise_scale launch");
 }
 
+// Z = A^T Q for A = f (d + c) (the transformed cube with its shift) and Q
+// (n x l) given as Q^T in bf16 hi / lo, [tn][np] K-major (rows >= l and
+// spectra >= n zero), with colsum[i] = sum_n Q[n, i]:
+//   Z[j, i] = f_j (sum_n d[n, j] Q[n, i] + c_j colsum[i]).
+__global__ void atq_assemble_kernel(const float* __restrict__ partial, int splits, int mb, int tn, int m, int l,
+                                    const float* __restrict__ c, const double* __restrict__ colsum,
+                                    const double* __restrict__ f, double* __restrict__ z) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  if (j >= m || i >= l) return;
+  const int ib = j / kTileM;
+  const int64_t off = ((int64_t)ib * kTileM + (j - ib * kTileM)) * tn + i;
+  const int64_t sstride = (int64_t)mb * kTileM * tn;
+  double acc = 0.0;
+  for (int s = 0; s < splits; ++s) acc += (double)partial[s * sstride + off];
+  acc += (double)c[j] * colsum[i];
+  z[(int64_t)j * l + i] = f ? acc * f[j] : acc;
+}
+
+fkk_status launch_atq(fkk_ctx* ctx, const DtLayout& L, const __nv_bfloat16* qt_hi, const __nv_bfloat16* qt_lo,
+                      int tn, int l, const double* colsum, const double* f, double* z, cudaStream_t st) {
+  if (tn != 64 && tn != 128) return fail(ctx, FKK_ERR_INVALID_ARG, "A^T Q: %d columns per tile", tn);
+  fkk_status s;
+  const int mb = L.mg / kTileM;
+  const int64_t nkb = L.np / kBK;
+  int64_t splits = ((int64_t)ctx->sm_count * 4 + mb - 1) / mb;
+  if (splits < (nkb + 95) / 96) splits = (nkb + 95) / 96;
+  if (splits > nkb) splits = nkb;
+  if (splits < 1) splits = 1;
+  float* partial = (float*)workspace(ctx, "atq_partial", (size_t)splits * mb * kTileM * tn * sizeof(float), &s);
+  if (!partial) return s;
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  const uint64_t row_bytes = (uint64_t)L.np * 2;
+  FKK_TRY(make_tmap_2d(ctx, &ta_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_hi, L.np, L.mg, row_bytes, kBK, kTileM,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &ta_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_lo, L.np, L.mg, row_bytes, kBK, kTileM,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tb_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)qt_hi, L.np, tn, row_bytes, kBK, tn,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tb_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)qt_lo, L.np, tn, row_bytes, kBK, tn,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+  GramArgs a{mb, mb, nkb, (int)splits, partial, ctx->d_status};
+  if (tn == 64) {
+    auto kern = gram_tc_kernel<64, true>;
+    FKK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<64>()));
+    FKK_COUNT_LAUNCH(); kern<<<dim3(mb, (unsigned)splits), 128, gram_smem<64>(), st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
+  } else {
+    auto kern = gram_tc_kernel<128, true>;
+    FKK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<128>()));
+    FKK_COUNT_LAUNCH(); kern<<<dim3(mb, (unsigned)splits), 128, gram_smem<128>(), st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
+  }
+  FKK_CUDA(ctx, cudaGetLastError());
+  FKK_COUNT_LAUNCH();
+  atq_assemble_kernel<<<L.m, ((l + 31) / 32) * 32, 0, st>>>(partial, (int)splits, mb, tn, L.m, l, L.c, colsum, f, z);
+  return cuda_check(ctx, cudaGetLastError(), "A^T Q assemble launch");
+}
+
 fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double* g, cudaStream_t st) {
   fkk_status s;
   const int mb = L.mg / kTileM;
@@ -258,9 +326,10 @@ fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double*
                        CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &tb_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L.dt_lo, L.np, L.mg, row_bytes, kBK, kTileN,
                        CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_CUDA(ctx, cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem));
+  auto kern = gram_tc_kernel<kTileN, false>;
+  FKK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<kTileN>()));
   GramArgs a{mb, ntiles, nkb, (int)splits, partial, ctx->d_status};
-  FKK_COUNT_LAUNCH(); gram_tc_kernel<<<dim3(ntiles, (unsigned)splits), 128, kGramSmem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
+  FKK_COUNT_LAUNCH(); kern<<<dim3(ntiles, (unsigned)splits), 128, gram_smem<kTileN>(), st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
   FKK_CUDA(ctx, cudaGetLastError());
   dim3 grid((L.m + 127) / 128, L.m);
   FKK_COUNT_LAUNCH(); gram_assemble_kernel<<<grid, 128, 0, st>>>(partial, (int)splits, ntiles, mb, L.m, L.n, L.c, L.sum_d, f, g);

@@ -979,6 +979,7 @@ __global__ void __launch_bounds__(kApThreads) wy_apply_kernel(const df* __restri
     z0[i] = z[(size_t)i * k + c0];
     z1[i] = has1 ? z[(size_t)i * k + c1] : dw::make(0.f);
   }
+  __syncthreads();  // every warp reads rows other warps loaded
   const int nbk = (nrefl + kWY - 1) / kWY;
   for (int b = nbk - 1; b >= 0; --b) {
     const int j0 = b * kWY, nr = min(kWY, nrefl - j0);
@@ -1105,48 +1106,64 @@ __global__ void ztz_kernel(const double* __restrict__ z, int m, int k, double* _
 }
 
 // One block: R (upper) with W = R^T R, then Rinv.  A pivot that has lost all
-// but 1e-20 of its column norm (linearly dependent vectors) is reported as
-// FKK_ERR_NOT_CONVERGED.
-__global__ void chol_inv_kernel(const double* __restrict__ w, int k, double* __restrict__ rinv,
-                                long long* status) {
+// but drop_tol of its column's squared norm (a linearly dependent vector):
+// strict -- reported as FKK_ERR_NOT_CONVERGED (pivot 1); otherwise the
+// column is dropped (its column and row of Rinv are 0).  The pivots are kept
+// as reciprocals (no division in the loops), and each entry of Rinv, formed
+// a row at a time from the bottom, has its dot product split over 8 threads.
+constexpr int kCholSplit = 8;
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ w, int k, double* __restrict__ rinv,
+                                                       long long* status, double drop_tol, int strict) {
   extern __shared__ double sm[];
-  double* r = sm;           // [k][k]
-  double* ri = r + k * k;   // [k][k]
+  double* r = sm;              // [k][k]
+  double* ri = r + k * k;      // [k][k]
+  double* dinv = ri + k * k;   // [k]: 1 / R[j][j], 0 for a dropped column
   for (int x = threadIdx.x; x < k * k; x += blockDim.x) {
     r[x] = w[x];
     ri[x] = 0.0;
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    __shared__ double piv;
     if (threadIdx.x == 0) {
       const double dj = r[j * k + j];
-      if (dj > 1e-20 * w[j * k + j] && dj < 1e300) {
-        piv = sqrt(dj);
-      } else {
+      double inv;
+      if (dj > drop_tol * w[j * k + j] && dj < 1e300) {
+        inv = rsqrt(dj);
+      } else if (strict) {
         record_error(status, kErrNotConverged);
-        piv = 1.0;
+        inv = 1.0;
+      } else {
+        inv = 0.0;  // drop: the row of R below is zeroed, and so is its Rinv
       }
-      r[j * k + j] = piv;
+      dinv[j] = inv;
     }
     __syncthreads();
-    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) r[j * k + q] /= piv;
+    const double inv = dinv[j];
+    for (int q = j + 1 + threadIdx.x; q < k; q += blockDim.x) r[j * k + q] *= inv;
     __syncthreads();
-    for (int x = threadIdx.x; x < (k - j - 1) * (k - j - 1); x += blockDim.x) {
-      const int q1 = j + 1 + x / (k - j - 1), q2 = j + 1 + x % (k - j - 1);
-      if (q2 >= q1) r[q1 * k + q2] -= r[j * k + q1] * r[j * k + q2];
+    // trailing update, a (16 x 16)-thread grid over (q1, q2), q2 >= q1
+    for (int q1 = j + 1 + (threadIdx.x >> 4); q1 < k; q1 += 16) {
+      const double a = r[j * k + q1];
+      for (int q2 = q1 + (threadIdx.x & 15); q2 < k; q2 += 16) r[q1 * k + q2] -= a * r[j * k + q2];
     }
     __syncthreads();
   }
-  // Rinv column by column (R upper triangular): R X = I
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    for (int p = c; p >= 0; --p) {
-      double s = p == c ? 1.0 : 0.0;
-      for (int q = p + 1; q <= c; ++q) s -= r[p * k + q] * ri[q * k + c];
-      ri[p * k + c] = s / r[p * k + p];
+  // Rinv[p][c] = dinv[p] (delta_pc - sum_{p < q <= c} R[p][q] Rinv[q][c]),
+  // R[p][q] (q > p) = R scaled row p -- rows from the bottom up
+  const int lane8 = threadIdx.x % kCholSplit, grp = threadIdx.x / kCholSplit;
+  const int ngrp = blockDim.x / kCholSplit;
+  for (int p = k - 1; p >= 0; --p) {
+    for (int c0 = p; c0 < k; c0 += ngrp) {
+      const int c = c0 + grp;
+      double sacc = 0.0;
+      if (c < k)
+        for (int q = p + 1 + lane8; q <= c; q += kCholSplit) sacc = fma(r[p * k + q], ri[q * k + c], sacc);
+#pragma unroll
+      for (int o = kCholSplit / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o, kCholSplit);
+      if (c < k && lane8 == 0) ri[p * k + c] = dinv[p] * ((p == c ? 1.0 : 0.0) - sacc);
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int x = threadIdx.x; x < k * k; x += blockDim.x) rinv[x] = ri[x];
 }
 
@@ -1295,15 +1312,45 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   if (!wk) return s;
   FKK_COUNT_LAUNCH();
   ztz_kernel<<<dim3(k, k), 128, 0, st>>>(vz, m, k, wk);
-  const size_t sc = (size_t)2 * k * k * sizeof(double);
+  const size_t sc = ((size_t)2 * k * k + k) * sizeof(double);
   FKK_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc));
   FKK_COUNT_LAUNCH();
-  chol_inv_kernel<<<1, 256, sc, st>>>(wk, k, wk + k * k, ctx->d_status);
+  chol_inv_kernel<<<1, 256, sc, st>>>(wk, k, wk + k * k, ctx->d_status, 1e-20, 1);
   FKK_COUNT_LAUNCH();
   apply_rinv_kernel<<<(m + 7) / 8, 256, 0, st>>>(vz, m, k, wk + k * k, v);
   FKK_COUNT_LAUNCH();
   sign_fix_kernel<<<k, 256, 0, st>>>(v, m, k, ctx->d_status);
   return cuda_check(ctx, cudaGetLastError(), "eigensolve");
+}
+
+// The fp64 Cholesky-QR pieces above, for other small m x k matrices.
+fkk_status launch_ztz(fkk_ctx* ctx, const double* z, int m, int k, double* w, cudaStream_t st) {
+  FKK_COUNT_LAUNCH();
+  ztz_kernel<<<dim3(k, k), 128, 0, st>>>(z, m, k, w);
+  return cuda_check(ctx, cudaGetLastError(), "ztz");
+}
+
+fkk_status launch_chol_inv(fkk_ctx* ctx, const double* w, int k, double* rinv, cudaStream_t st, double drop_tol,
+                           bool strict) {
+  const size_t sc = ((size_t)2 * k * k + k) * sizeof(double);
+  if (sc > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "Cholesky of %d x %d does not fit shared memory", k, k);
+  FKK_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc));
+  FKK_COUNT_LAUNCH();
+  chol_inv_kernel<<<1, 256, sc, st>>>(w, k, rinv, ctx->d_status, drop_tol, strict ? 1 : 0);
+  return cuda_check(ctx, cudaGetLastError(), "chol_inv");
+}
+
+fkk_status launch_apply_rinv(fkk_ctx* ctx, const double* z, int m, int k, const double* rinv, double* v,
+                             cudaStream_t st) {
+  FKK_COUNT_LAUNCH();
+  apply_rinv_kernel<<<(m + 7) / 8, 256, 0, st>>>(z, m, k, rinv, v);
+  return cuda_check(ctx, cudaGetLastError(), "apply_rinv");
+}
+
+fkk_status launch_sign_fix(fkk_ctx* ctx, double* v, int m, int k, cudaStream_t st) {
+  FKK_COUNT_LAUNCH();
+  sign_fix_kernel<<<k, 256, 0, st>>>(v, m, k, ctx->d_status);
+  return cuda_check(ctx, cudaGetLastError(), "sign_fix");
 }
 
 }  // namespace fkk
