@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cube of synth.CONFIGS to fit (the benchmark workload by default; a smaller one keeps "
                          "profiler captures small)")
+    ap.add_argument("--svd", default="exact", choices=["exact", "randomized"],
+                    help="factorisation of A in the timed fit: the Gram matrix and its eigensolve, or the "
+                         "randomised SVD (10 oversampling columns, 2 power iterations)")
     return ap.parse_args()
 
 
@@ -158,11 +161,23 @@ STAGE_KERNEL = {  # stage -> (kernel, sources, bound)
 }
 
 
-def algorithmic_work(stage, n, m, k):
+RSVD_POWER_ITERS = 2
+RSVD_STAGE = ("rsvd passes over A (project_tc_kernel, gram_tc_kernel<64,1>)",
+              ["rsvd.cu", "gram.cu", "project_tc.cu", "tc.cuh", "common.cuh"], "hbm")
+
+
+def algorithmic_work(stage, n, m, k, svd="exact"):
     """Algorithmic bytes (hbm) or flops (tensor / alu) of one launch of the
-    stage's dominant kernel for n spectra, m channels, k basis vectors."""
+    stage's dominant kernel for n spectra, m channels, k basis vectors.  With
+    the randomised SVD the factorisation stage is 2q + 2 reads of the
+    transformed cube (A Omega, q times A^T Q and A Q, and the final A^T Q)."""
     mg = -(-m // 256) * 256
     np_ = -(-n // 64) * 64
+    if svd == "randomized":
+        if stage == "gram":
+            return None
+        if stage == "eig":
+            return (2 * RSVD_POWER_ITERS + 2) * 2 * 2.0 * np_ * mg
     if stage == "transform":
         return 4.0 * n * m + 2 * 2.0 * np_ * mg  # read I (fp32), write two bf16 terms
     if stage == "gram":
@@ -280,7 +295,9 @@ def run_ours(args, rank, world, local):
     x = torch.from_numpy(cube.i_cars).cuda()
     ref = torch.from_numpy(cube.i_ref).cuda()
     out = torch.empty_like(x)
-    prm = fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g)
+    svd = fk.SVD_RANDOMIZED if args.svd == "randomized" else fk.SVD_EXACT
+    prm = fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g, svd=svd,
+                        rsvd_power_iters=RSVD_POWER_ITERS)
 
     def step():
         b, _, _ = fk.fkk_fit_basis(ctx, x, ref, prm, im_out=out, stream=st)
@@ -336,10 +353,10 @@ def run_ours(args, rank, world, local):
     pk = peaks()
     # the largest stage that has a work model (the basis math is a chain of
     # small latency-bound kernels without one)
-    modelled = [st_ for st_ in stage_acc if algorithmic_work(st_, n, m, K_BASIS) is not None]
+    modelled = [st_ for st_ in stage_acc if algorithmic_work(st_, n, m, K_BASIS, args.svd) is not None]
     stage = max(modelled, key=stage_acc.get)
-    kernel, srcs, bound = STAGE_KERNEL[stage]
-    work = algorithmic_work(stage, n, m, K_BASIS)
+    kernel, srcs, bound = RSVD_STAGE if (args.svd == "randomized" and stage == "eig") else STAGE_KERNEL[stage]
+    work = algorithmic_work(stage, n, m, K_BASIS, args.svd)
     t_s = stage_acc[stage] / 1e3
     if bound == "hbm":
         peak = pk["hbm_gbs"] if pk else 6800.0
@@ -373,6 +390,7 @@ def run_ours(args, rank, world, local):
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_spectra": n, "n_channels": m, "k": K_BASIS, "pec": True, "sec": True,
+                   "svd": args.svd if args.svd == "exact" else f"randomized (p = 10, q = {RSVD_POWER_ITERS})",
                    "noise": "poisson+gauss snr20", "l2": "inputs (2.81 GB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "stage_ms": stage_acc,
@@ -432,6 +450,18 @@ def run_ours(args, rank, world, local):
                                    "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9}
         line["apply"] = {"value": n / (ap_ms / 1e3), "unit": "spectra/s", "ms": ap_ms,
                          "hbm_gbs": 8.0 * n * m / (ap_ms / 1e3) / 1e9}
+        # the same fit with the randomised SVD (Sec. 5) in place of the Gram
+        # matrix and its eigensolve, at 2 and 1 power iterations
+        line["randomized_svd"] = {}
+        for q in (2, 1):
+            rp = fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g,
+                               svd=fk.SVD_RANDOMIZED, rsvd_power_iters=q)
+            made = []
+            r_ms = timed(lambda: made.append(fk.fkk_fit_basis(ctx, x, ref, rp, im_out=out, stream=st)[0]))
+            for b in made:
+                b.close()
+            line["randomized_svd"][f"q{q}"] = {"value": world * n / (r_ms / 1e3), "unit": "spectra/s",
+                                               "ms_per_step": r_ms, "oversample": 10, "power_iters": q}
         # the conventional per-spectrum workflow (KK, ALS phase-error
         # correction, Savitzky-Golay scale-error correction) the paper
         # measures the factorised method against, on the same cube
