@@ -162,6 +162,8 @@ typedef struct {
   int32_t rsvd_oversample;   /* randomised: l = k + oversample test vectors (l <= 80) */
   int32_t rsvd_power_iters;  /* randomised: subspace iterations, 0..20 */
   uint64_t rsvd_seed;        /* randomised: key of the Philox4x64-10 test matrix */
+  int32_t denoise_k;    /* conventional_per_spectrum only: 0 no denoising; > 0 (<= 80) keep that many
+                           singular vectors of the raw spectra; < 0 the rank rule (at most k_max) */
 } fkk_fit_params;
 
 /* How fkk_fit_basis finds V_k and s:
@@ -188,7 +190,7 @@ fkk_status fkk_philox_normals(fkk_ctx* ctx, int64_t count, uint64_t seed, double
  * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
  * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
  * k_max 80, rank_eps 0 (FLT_EPSILON), svd EXACT, rsvd_oversample 10,
- * rsvd_power_iters 2, rsvd_seed 0.
+ * rsvd_power_iters 2, rsvd_seed 0, denoise_k 0.
  *
  * k = 0 selects the number of basis vectors by the rank rule of Sec. 4.1:
  * the count of singular values s_i > s_1 * max(N, M) * rank_eps (the NumPy /
@@ -279,8 +281,19 @@ fkk_status fkk_basis_get(const fkk_basis* basis, int32_t which, double* host_dst
 /* Conventional workflow: per-spectrum KK, PEC and SEC (Sec. 2.1)       */
 /* ------------------------------------------------------------------ */
 
-/* The conventional per-spectrum workflow of Fig. 1(a) (after its denoising
- * step), Eq. KCARS_from_K, for every spectrum n:
+/* The conventional per-spectrum workflow of Fig. 1(a), Eq. KCARS_from_K.
+ * With params->denoise_k != 0 the raw spectra X (n_spectra x n_channels)
+ * are first replaced by their truncated SVD (the workflow's denoising step;
+ * Sec. 2.2: drop the singular vectors that carry noise):
+ *   X^T X = V diag(lambda) V^T (tensor-core Gram of X - c with c the mean
+ *             of the first 256 rows, exact in its shift; the double-word
+ *             eigensolver of fkk_fit_basis),
+ *   X_k     = (X V_k) V_k^T, k = denoise_k, or for denoise_k < 0 the rank
+ *             rule of fkk_fit_basis (s_i > s_1 max(N, M) rank_eps, at most
+ *             k_max) -- a synchronisation of `stream`.
+ * It holds the n_spectra x n_channels denoised cube and the transformed
+ * cube (4 bytes per element) in the context's workspace.  Then, for every
+ * spectrum n:
  *   a       = 1/2 ln max(I_CARS[n,:] / I_ref, ratio_floor),  phi = H{a}
  *             (the discrete Hilbert transform of kk_per_spectrum)
  *   phi_err = D{phi} if params->pec, else 0: the asymmetric least squares
@@ -294,12 +307,13 @@ fkk_status fkk_basis_get(const fkk_basis* basis, int32_t which, double* host_dst
  *             the mean over the channels (sec_mode FKK_SEC_MEAN)
  * im_out (required) and re_out (may be NULL) receive Im and Re K_CARS.
  * Uses pad_len (power of two in [M, 4096]; 0 = nextpow2(2M)), pec, sec,
- * als_*, sec_mode, sg_window, sg_order and ratio_floor of *params; the other
- * fields are ignored.  n_channels in [8, 2048].  Device arrays, row-major,
- * row strides ld / ld_out.  Works in chunks of spectra inside a context
- * workspace of about 32 M bytes per spectrum of a chunk (a chunk is halved
- * until it fits the context's budget).  Clamped ratios are counted as by
- * kk_per_spectrum.  Asynchronous on `stream`. */
+ * als_*, sec_mode, sg_window, sg_order, ratio_floor, denoise_k, k_max and
+ * rank_eps of *params; the other fields are ignored.  n_channels in
+ * [8, 2048]; denoise_k <= min(80, n_channels, n_spectra).  Device arrays,
+ * row-major, row strides ld / ld_out.  Works in chunks of spectra inside a
+ * context workspace of about 32 M bytes per spectrum of a chunk (a chunk is
+ * halved until it fits the context's budget).  Clamped ratios are counted
+ * as by kk_per_spectrum.  Asynchronous on `stream` (but see denoise_k < 0). */
 fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels,
                                      int64_t ld, const float* i_ref, const fkk_fit_params* params, float* im_out,
                                      float* re_out, int64_t ld_out, void* stream);

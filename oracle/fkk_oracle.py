@@ -6,7 +6,8 @@ point and the benchmark's CPU-baseline / reference legs may import it; the
 product path never does.  It shares no code with the CUDA library.
 
 Everything is float64 numpy.  Library primitives used as single steps: FFT
-(numpy.fft), symmetric eigendecomposition (numpy.linalg.eigh), dense and
+(numpy.fft), symmetric eigendecomposition (numpy.linalg.eigh), the SVD
+(numpy.linalg.svd, for the conventional workflow's denoising), dense and
 banded linear solves (numpy.linalg.solve, scipy.linalg.solveh_banded), and
 matrix products.
 
@@ -68,6 +69,8 @@ class FitParams:
     rsvd_oversample: int = 10
     rsvd_power_iters: int = 2
     rsvd_seed: int = 0
+    denoise_k: int = 0       # conventional workflow: 0 no SVD denoising of the raw spectra; > 0 keep that
+                             # many singular triplets; < 0 the rank rule (at most k_max)
 
 
 def pad_len(n_channels: int) -> int:
@@ -175,10 +178,26 @@ def conventional_from_phase(a, phi, params: "FitParams", L: int | None = None):
     return re / div, im / div
 
 
+def svd_denoise(i_cars, k: int, k_max: int = 80, eps: float = 0.0):
+    """The denoising step of the conventional workflow (Fig. 1(a); Sec. 2.2:
+    drop the singular vectors that carry noise): the truncated SVD of the raw
+    spectra (rows = spectra), U_k S_k V_k^T with the k largest singular
+    values, or with k < 0 the rank rule of Sec. 4.1 (at most k_max).
+    Returns (denoised spectra, k)."""
+    X = np.asarray(i_cars, F64)
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    if k < 0:
+        k = rank_k(s * s, X.shape[0], X.shape[1], k_max, eps)
+    k = min(k, s.size)
+    return (U[:, :k] * s[:k]) @ Vt[:k], k
+
+
 def conventional(i_cars, i_ref, params: "FitParams", L: int | None = None):
-    """The conventional workflow of Fig. 1(a) (without its denoising SVD):
-    per-spectrum KK (Eq. K), then PEC and SEC (Eq. KCARS_from_K).
-    Returns (Re K_CARS, Im K_CARS)."""
+    """The conventional workflow of Fig. 1(a): optionally the SVD denoising
+    of the raw spectra (params.denoise_k), then per-spectrum KK (Eq. K),
+    PEC and SEC (Eq. KCARS_from_K).  Returns (Re K_CARS, Im K_CARS)."""
+    if params.denoise_k:
+        i_cars, _ = svd_denoise(i_cars, params.denoise_k, params.k_max, params.rank_eps)
     a = log_ratio(i_cars, i_ref, None, params.ratio_floor)
     phi = hilbert(a, L or params.pad_len or None)
     return conventional_from_phase(a, phi, params, L or params.pad_len or None)

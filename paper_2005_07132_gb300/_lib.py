@@ -92,6 +92,7 @@ class FitParams(C.Structure):
         ("k_max", C.c_int32), ("rank_eps", C.c_double),
         ("svd", C.c_int32), ("rsvd_oversample", C.c_int32), ("rsvd_power_iters", C.c_int32),
         ("rsvd_seed", C.c_uint64),
+        ("denoise_k", C.c_int32),
     ]
 
 

@@ -268,6 +268,7 @@ void fkk_fit_params_default(fkk_fit_params* p) {
   p->rsvd_oversample = 10;
   p->rsvd_power_iters = 2;
   p->rsvd_seed = 0;
+  p->denoise_k = 0;
 }
 
 fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m, int64_t ld, const float* i_ref,

@@ -1,6 +1,6 @@
-// The conventional per-spectrum workflow (Sec. 2.1 and Fig. 1(a) after its
-// denoising step; Eq. KCARS_from_K), the baseline the factorised method is
-// measured against:
+// The conventional per-spectrum workflow (Sec. 2.1 and Fig. 1(a);
+// Eq. KCARS_from_K), the baseline the factorised method is measured against:
+//   X       <- X_k, the truncated SVD of the raw spectra        (optional)
 //   a       = 1/2 ln max(I/I_ref, floor),  phi = H{a}              (Eq. K)
 //   phi_err = D{phi}, the asymmetric-least-squares baseline         (PEC)
 //   K_pec   = exp(a + H{phi_err}) exp(i (phi - phi_err))
@@ -22,8 +22,11 @@
 //      with the first / last full window's polynomial at the edges; or the
 //      mean -- and writes Im (and Re) K_CARS.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
+#include <vector>
 
+#include "common.cuh"
 #include "df64.cuh"
 #include "fft.cuh"
 #include "fit.h"
@@ -406,6 +409,95 @@ size_t finish_smem_bytes(int L, int M, int nfft) {
          (size_t)nfft * kFinWarps * 12 * sizeof(float);
 }
 
+
+// Vt (k x m) = V^T for V (m x k, row stride ldv).
+__global__ void transpose_v_kernel(const double* __restrict__ v, int m, int k, int ldv, double* __restrict__ vt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * k) return;
+  const int i = (int)(t / m), j = (int)(t % m);
+  vt[t] = v[(int64_t)j * ldv + i];
+}
+
+// b = V V^T c (m), one block: the shift's share of X_k = (D + 1 c^T) V V^T.
+__global__ void shift_share_kernel(const double* __restrict__ v, const float* __restrict__ c, int m, int k,
+                                   float* __restrict__ b) {
+  __shared__ double t[80];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = w; i < k; i += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < m; j += 32) acc += (double)c[j] * v[(int64_t)j * k + i];
+    acc = warp_sum(acc);
+    if (lane == 0) t[i] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += v[(int64_t)j * k + i] * t[i];
+    b[j] = (float)acc;
+  }
+}
+
+// The conventional workflow's denoising step (Fig. 1(a); Sec. 2.2): the
+// truncated SVD X_k = (X V_k) V_k^T of the raw spectra X (n x m), V_k the k
+// leading eigenvectors of X^T X.  The Gram matrix, the eigensolver, the
+// projection and the reconstruction are the fit's kernels, the transform in
+// its raw mode (D = X - 1 c^T) and the reconstruction with its linear
+// epilogue.  Raw spectra are dominated by their mean, so the tensor cores
+// see only D: X_k = (D V_k) V_k^T + 1 (V_k V_k^T c)^T, the second term
+// exact in fp64 and added per channel.
+// *out: n x m (row stride m) in the context's workspace.
+fkk_status svd_denoise(fkk_ctx* ctx, const float* x, int64_t n, int m, int64_t ld, const fkk_fit_params& pp,
+                       float** out, cudaStream_t st) {
+  fkk_status s;
+  DtLayout D;
+  FKK_TRY(launch_transform(ctx, x, n, m, ld, nullptr, 0.f, D, st, true));
+  double* G = (double*)workspace(ctx, "dn_gram", (size_t)m * m * 8, &s);
+  if (!G) return s;
+  FKK_TRY(launch_gram(ctx, D, nullptr, G, st));
+  const bool rule = pp.denoise_k < 0;
+  const int ke = rule ? std::min(pp.k_max, m) : pp.denoise_k;  // eigenpairs computed
+  double* lam = (double*)workspace(ctx, "dn_lam", (size_t)ke * 8, &s);
+  if (!lam) return s;
+  double* v = (double*)workspace(ctx, "dn_v", (size_t)m * ke * 8, &s);
+  if (!v) return s;
+  FKK_TRY(launch_eig_topk(ctx, G, m, ke, lam, v, st));
+  int k = ke;
+  if (rule) {  // the rank rule of Sec. 4.1, as fkk_fit_basis applies it
+    std::vector<double> lh(ke);
+    FKK_CUDA(ctx, cudaMemcpyAsync(lh.data(), lam, (size_t)ke * 8, cudaMemcpyDeviceToHost, st));
+    FKK_CUDA(ctx, cudaStreamSynchronize(st));
+    const double eps = pp.rank_eps > 0.0 ? pp.rank_eps : (double)FLT_EPSILON;
+    const double tol = std::sqrt(std::max(lh[0], 0.0)) * (double)std::max<int64_t>(n, m) * eps;
+    k = 0;
+    while (k < ke && std::sqrt(std::max(lh[k], 0.0)) > tol) ++k;
+    if (k < 1) k = 1;
+  }
+  double* vk = v;
+  if (k < ke) {  // the projection reads V_k with row stride k
+    vk = (double*)workspace(ctx, "dn_vk", (size_t)m * k * 8, &s);
+    if (!vk) return s;
+    FKK_CUDA(ctx, cudaMemcpy2DAsync(vk, (size_t)k * 8, v, (size_t)ke * 8, (size_t)k * 8, m, cudaMemcpyDeviceToDevice, st));
+  }
+  float* P = (float*)workspace(ctx, "dn_p", (size_t)n * k * 4, &s);
+  if (!P) return s;
+  DtLayout Dv = D;
+  Dv.c = nullptr;  // P = D V_k, without the shift's offset
+  FKK_TRY(launch_project(ctx, Dv, vk, nullptr, k, P, nullptr, nullptr, st));
+  float* b = (float*)workspace(ctx, "dn_bias", (size_t)m * 4, &s);
+  if (!b) return s;
+  FKK_COUNT_LAUNCH(); shift_share_kernel<<<1, 256, 0, st>>>(vk, D.c, m, k, b);
+  double* vt = (double*)workspace(ctx, "dn_vt", (size_t)m * k * 8, &s);
+  if (!vt) return s;
+  const int64_t tot = (int64_t)m * k;
+  FKK_COUNT_LAUNCH(); transpose_v_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(vk, m, k, k, vt);
+  FKK_CUDA(ctx, cudaGetLastError());
+  float* xk = (float*)workspace(ctx, "dn_out", (size_t)n * m * 4, &s);
+  if (!xk) return s;
+  FKK_TRY(launch_reconstruct_linear(ctx, P, n, k, m, vt, b, xk, m, st));
+  *out = xk;
+  return FKK_OK;
+}
+
 }  // namespace
 }  // namespace fkk
 
@@ -451,10 +543,20 @@ extern "C" fkk_status conventional_per_spectrum(fkk_ctx* ctx, const float* i_car
       return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: bad sec_mode");
     }
   }
+  if (pp.denoise_k > 0 && (pp.denoise_k > 80 || pp.denoise_k > m || pp.denoise_k > n_spectra))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: denoise_k %d exceeds min(80, M, N)", pp.denoise_k);
+  if (pp.denoise_k < 0 && (pp.k_max < 1 || pp.k_max > 80 || pp.k_max > n_spectra || !(pp.rank_eps >= 0.0)))
+    return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: rank rule needs 1 <= k_max <= min(80, N), rank_eps >= 0");
   if (n_spectra == 0) return FKK_OK;
   if (!i_cars || !i_ref || !im_out) return fail(ctx, FKK_ERR_INVALID_ARG, "conventional_per_spectrum: null pointer");
   FKK_TRY(bind(ctx));
   cudaStream_t st = as_stream(stream);
+  if (pp.denoise_k) {
+    float* xk = nullptr;
+    FKK_TRY(svd_denoise(ctx, i_cars, n_spectra, m, ld, pp, &xk, st));
+    i_cars = xk;
+    ld = m;
+  }
   const double lam = pp.als_lambda > 0.0 ? pp.als_lambda : 1e4 * std::pow(m / 1000.0, 4);
 
   // finish-kernel launch shape (as the KK kernel: one FFT per tpf threads)

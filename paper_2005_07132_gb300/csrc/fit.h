@@ -38,8 +38,10 @@ struct TransformArgs {
   long long* status;
 };
 
+// raw = false: d = 1/2 ln(max(I/I_ref, floor)) - c (the fit's A before f);
+// raw = true: d = I - c, the raw spectra (c the mean of the first rows).
 fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
-                            const float* i_ref, float floor_, DtLayout& L, cudaStream_t st);
+                            const float* i_ref, float floor_, DtLayout& L, cudaStream_t st, bool raw = false);
 
 // G = diag(f) (D^T D + s c^T + c s^T + N c c^T) diag(f), fp64, m x m (ld m).
 // f == nullptr means f = 1.
@@ -104,6 +106,12 @@ fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmi
 // Out = exp(P C_amp) sin(P C_ph) (and cos for re_out), P n x k fp32.
 fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
                               const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
+
+// Out = P C + 1 b^T (n x m, ld_out), C k x m fp64 row-major, b m floats or
+// null: the linear epilogue of the same tensor-core kernel (the SVD
+// denoising's X_k = (X V_k) V_k^T, with the shift's share in b).
+fkk_status launch_reconstruct_linear(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c,
+                                     const float* bias, float* out, int64_t ld_out, cudaStream_t st);
 
 // Same, on the tensor cores (bf16 x3 operands, exp / sin epilogue), k <= 128.
 fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,

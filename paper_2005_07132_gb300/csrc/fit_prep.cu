@@ -1,4 +1,5 @@
-// Transform pass of the fit: d = 1/2 ln(max(I/I_ref, floor)) - c, stored
+// Transform pass of the fit: d = 1/2 ln(max(I/I_ref, floor)) - c (or, in
+// raw mode for the conventional workflow's SVD denoising, d = I - c), stored
 // channel-major as two bf16 terms (D^T_hi, D^T_lo), plus per-channel sums of
 // d and of I.  c is a per-channel shift (the mean log ratio of the first
 // rows); it leaves A^T A unchanged in exact arithmetic,
@@ -13,22 +14,28 @@ namespace {
 constexpr int kShiftRows = 256;
 
 __global__ void shift_kernel(const float* __restrict__ i_cars, int64_t n, int m, int64_t ld,
-                             const float* __restrict__ i_ref, float floor_, float* __restrict__ c) {
+                             const float* __restrict__ i_ref, float floor_, float* __restrict__ c, int raw) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   int rows = (int)(n < kShiftRows ? n : kShiftRows);
-  float r = i_ref[j];
   double acc = 0.0;
-  for (int t = 0; t < rows; ++t) {
-    float x = i_cars[(int64_t)t * ld + j] / r;
-    x = (x >= floor_) ? x : floor_;
-    acc += 0.5f * logf(x);
+  if (raw) {
+    for (int t = 0; t < rows; ++t) acc += i_cars[(int64_t)t * ld + j];
+  } else {
+    const float r = i_ref[j];
+    for (int t = 0; t < rows; ++t) {
+      float x = i_cars[(int64_t)t * ld + j] / r;
+      x = (x >= floor_) ? x : floor_;
+      acc += 0.5f * logf(x);
+    }
   }
   c[j] = rows ? (float)(acc / rows) : 0.f;
 }
 
 // Block = 256 threads, tile = 64 rows x 64 channels; blockIdx.y = channel
 // tile; blockIdx.x walks row tiles rt = blockIdx.x, +gridDim.x, ...
+// kRaw: d = I - c (raw spectra; i_ref and the floor are not used).
+template <bool kRaw>
 __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   __shared__ float tile[64][65];
   __shared__ double red_d[4][64];
@@ -38,7 +45,7 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
   const int j0 = blockIdx.y * 64;
   const int j = j0 + tx;
   const bool jvalid = j < p.m;
-  const float rinv = jvalid ? 1.f / p.i_ref[j] : 1.f;
+  const float rinv = (jvalid && !kRaw) ? 1.f / p.i_ref[j] : 1.f;
   const float cj = jvalid ? p.c[j] : 0.f;
   const int64_t nrt = p.np / 64;
   double sum_d = 0.0, sum_i = 0.0, sum_d2 = 0.0;
@@ -60,9 +67,13 @@ __global__ void __launch_bounds__(256) transform_kernel(TransformArgs p) {
       float d = 0.f;
       if (jvalid && n < p.n) {
         const float v = vals[u];
-        float x = v * rinv;
-        if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
-        d = 0.5f * logf(x) - cj;
+        if (kRaw) {
+          d = v - cj;
+        } else {
+          float x = v * rinv;
+          if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
+          d = 0.5f * logf(x) - cj;
+        }
         td += d;
         td2 = fmaf(d, d, td2);
         ti += v;
@@ -122,7 +133,7 @@ __global__ void colsum_reduce_kernel(const double* __restrict__ part_d, const do
 }  // namespace
 
 fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
-                            const float* i_ref, float floor_, DtLayout& L, cudaStream_t st) {
+                            const float* i_ref, float floor_, DtLayout& L, cudaStream_t st, bool raw) {
   fkk_status s;
   L.n = n;
   L.m = m;
@@ -153,9 +164,13 @@ fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m,
   if (!part_i) return s;
   double* part_d2 = (double*)workspace(ctx, "part_d2", (size_t)grows * m * 8, &s);
   if (!part_d2) return s;
-  FKK_COUNT_LAUNCH(); shift_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_cars, n, m, ld, i_ref, floor_, L.c);
+  FKK_COUNT_LAUNCH(); shift_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_cars, n, m, ld, i_ref, floor_, L.c, raw ? 1 : 0);
   TransformArgs a{i_cars, n, m, ld, i_ref, floor_, L.c, L.np, L.dt_hi, L.dt_lo, part_d, part_i, part_d2, ctx->d_status};
-  FKK_COUNT_LAUNCH(); transform_kernel<<<dim3((unsigned)grows, ctiles), 256, 0, st>>>(a);
+  FKK_COUNT_LAUNCH();
+  if (raw)
+    transform_kernel<true><<<dim3((unsigned)grows, ctiles), 256, 0, st>>>(a);
+  else
+    transform_kernel<false><<<dim3((unsigned)grows, ctiles), 256, 0, st>>>(a);
   FKK_COUNT_LAUNCH();
   colsum_reduce_kernel<<<(m + 127) / 128, 128, 0, st>>>(part_d, part_i, part_d2, (int)grows, m, L.sum_d, L.sum_i,
                                                         L.sum_d2);

@@ -37,11 +37,15 @@ struct ReconArgs {
   float* re;
   int64_t ld_out;
   long long* status;
+  const float* bias;  // linear mode: added to channel j of every row (may be null)
 };
 
 __device__ __forceinline__ uint32_t a_bytes(int kp) { return kTM * kp * 2; }
 __device__ __forceinline__ uint32_t b_bytes(int kp) { return kTN * kp * 2; }
 
+// kLinear: the output is the amplitude accumulator itself plus a per-channel
+// bias (P C + 1 b^T), with no exp / sin and no Re output.
+template <bool kLinear>
 __global__ void __launch_bounds__(kRecThreads, 1)
     recon_tc_kernel(const __grid_constant__ CUtensorMap tp_hi, const __grid_constant__ CUtensorMap tp_lo,
                     const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,
@@ -183,18 +187,24 @@ __global__ void __launch_bounds__(kRecThreads, 1)
             tc::tmem_ld32(taddr + c64 * 64 + hh * 32, v);
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-              float sn;
-              __sincosf(v[2 * t + 1], &sn, &cs[hh * 16 + t]);
-              ex[hh * 16 + t] = __expf(v[2 * t]);
-              tbuf[lane * 33 + hh * 16 + t] = ex[hh * 16 + t] * sn;
+              if (kLinear) {
+                tbuf[lane * 33 + hh * 16 + t] = v[2 * t];
+              } else {
+                float sn;
+                __sincosf(v[2 * t + 1], &sn, &cs[hh * 16 + t]);
+                ex[hh * 16 + t] = __expf(v[2 * t]);
+                tbuf[lane * 33 + hh * 16 + t] = ex[hh * 16 + t] * sn;
+              }
             }
           }
           __syncwarp();
           const int j = ct * (kTN / 2) + c64 * 32 + lane;  // this lane's channel
-          if (j < p.m)
-            for (int r = 0; r < rows; ++r) p.im[(n0 + r) * p.ld_out + j] = tbuf[r * 33 + lane];
+          if (j < p.m) {
+            const float bj = (kLinear && p.bias) ? p.bias[j] : 0.f;
+            for (int r = 0; r < rows; ++r) p.im[(n0 + r) * p.ld_out + j] = tbuf[r * 33 + lane] + bj;
+          }
           __syncwarp();
-          if (p.re) {
+          if (!kLinear && p.re) {
 #pragma unroll
             for (int t = 0; t < 32; ++t) tbuf[lane * 33 + t] = ex[t] * cs[t];
             __syncwarp();
@@ -251,55 +261,10 @@ size_t recon_smem(int kp, int nst) {
          (size_t)kEpiWarps * 32 * 33 * sizeof(float);
 }
 
-}  // namespace
-
-fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
-                                 const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st) {
-  fkk_status s;
-  if (k > 128) return fail(ctx, FKK_ERR_INVALID_ARG, "k > 128");
-  const int kp = k <= 64 ? 64 : 128;
-  const int64_t n_pad = ((n + kTM - 1) / kTM) * kTM;
-  const int rows_c = ((2 * m + kTN - 1) / kTN) * kTN;
-  __nv_bfloat16* phi = (__nv_bfloat16*)workspace(ctx, "rtc_phi", (size_t)n_pad * kp * 2, &s);
-  if (!phi) return s;
-  __nv_bfloat16* plo = (__nv_bfloat16*)workspace(ctx, "rtc_plo", (size_t)n_pad * kp * 2, &s);
-  if (!plo) return s;
-  __nv_bfloat16* chi = (__nv_bfloat16*)workspace(ctx, "rtc_chi", (size_t)rows_c * kp * 2, &s);
-  if (!chi) return s;
-  __nv_bfloat16* clo = (__nv_bfloat16*)workspace(ctx, "rtc_clo", (size_t)rows_c * kp * 2, &s);
-  if (!clo) return s;
-  {
-    const int64_t tot = n_pad * kp;
-    FKK_COUNT_LAUNCH();
-    pack_p_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p, n, k, n_pad, kp, phi, plo);
-    const int64_t totc = (int64_t)rows_c * kp;
-    FKK_COUNT_LAUNCH();
-    pack_c_kernel<<<(unsigned)((totc + 255) / 256), 256, 0, st>>>(c_amp, c_ph, k, m, rows_c, kp, chi, clo);
-    FKK_CUDA(ctx, cudaGetLastError());
-  }
-  CUtensorMap tph, tpl, tch, tcl;
-  const uint64_t rb = (uint64_t)kp * 2;
-  FKK_TRY(make_tmap_2d(ctx, &tph, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, phi, kp, n_pad, rb, 64, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_TRY(make_tmap_2d(ctx, &tpl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, plo, kp, n_pad, rb, 64, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_TRY(make_tmap_2d(ctx, &tch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, chi, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_TRY(make_tmap_2d(ctx, &tcl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, clo, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
-  int nst = 2;
-  if (recon_smem(kp, nst) > 227 * 1024) nst = 1;
-  const size_t smem = recon_smem(kp, nst);
-  if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "reconstruction tile does not fit shared memory");
-  FKK_CUDA(ctx, cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ReconArgs a{n, m, kp, (int)(n_pad / kTM), rows_c / kTN, nst, im, re, ld_out, ctx->d_status};
-  const int grid = (int)std::min<int64_t>(ctx->sm_count, a.n_row_tiles);
-  FKK_COUNT_LAUNCH();
-  recon_tc_kernel<<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
-  return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
-}
-
-fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n, int k, int m,
-                                         const double* c_amp, const double* c_ph, float* im, float* re,
-                                         int64_t ld_out, cudaStream_t st, void* p_hi, void* p_lo, void* c_hi,
-                                         void* c_lo) {
-  if (k > 128) return fail(ctx, FKK_ERR_INVALID_ARG, "k > 128");
+// Packs P and C into the given scratch and launches the kernel.
+fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                        const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st, void* p_hi,
+                        void* p_lo, void* c_hi, void* c_lo, bool linear, const float* bias) {
   const int kp = k <= 64 ? 64 : 128;
   const int64_t n_pad = ((n + kTM - 1) / kTM) * kTM;
   const int rows_c = ((2 * m + kTN - 1) / kTN) * kTN;
@@ -326,12 +291,61 @@ fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n
   if (recon_smem(kp, nst) > 227 * 1024) nst = 1;
   const size_t smem = recon_smem(kp, nst);
   if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "reconstruction tile does not fit shared memory");
-  FKK_CUDA(ctx, cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ReconArgs a{n, m, kp, (int)(n_pad / kTM), rows_c / kTN, nst, im, re, ld_out, ctx->d_status};
+  const void* fn = linear ? (const void*)recon_tc_kernel<true> : (const void*)recon_tc_kernel<false>;
+  FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ReconArgs a{n,      m,
+              kp,     (int)(n_pad / kTM),
+              rows_c / kTN, nst,
+              im,     linear ? nullptr : re,
+              ld_out, ctx->d_status,
+              linear ? bias : nullptr};
   const int grid = (int)std::min<int64_t>(ctx->sm_count, a.n_row_tiles);
   FKK_COUNT_LAUNCH();
-  recon_tc_kernel<<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
+  if (linear)
+    recon_tc_kernel<true><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
+  else
+    recon_tc_kernel<false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
   return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
+}
+
+// The packed operands in the context's workspace.
+fkk_status recon_tc_ws(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                       const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st, bool linear,
+                       const float* bias) {
+  fkk_status s;
+  if (k > 128) return fail(ctx, FKK_ERR_INVALID_ARG, "k > 128");
+  const int kp = k <= 64 ? 64 : 128;
+  const int64_t n_pad = ((n + kTM - 1) / kTM) * kTM;
+  const int rows_c = ((2 * m + kTN - 1) / kTN) * kTN;
+  void* phi = workspace(ctx, "rtc_phi", (size_t)n_pad * kp * 2, &s);
+  if (!phi) return s;
+  void* plo = workspace(ctx, "rtc_plo", (size_t)n_pad * kp * 2, &s);
+  if (!plo) return s;
+  void* chi = workspace(ctx, "rtc_chi", (size_t)rows_c * kp * 2, &s);
+  if (!chi) return s;
+  void* clo = workspace(ctx, "rtc_clo", (size_t)rows_c * kp * 2, &s);
+  if (!clo) return s;
+  return recon_tc_run(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, st, phi, plo, chi, clo, linear, bias);
+}
+
+}  // namespace
+
+fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                                 const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st) {
+  return recon_tc_ws(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, st, false, nullptr);
+}
+
+fkk_status launch_reconstruct_linear(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c,
+                                     const float* bias, float* out, int64_t ld_out, cudaStream_t st) {
+  return recon_tc_ws(ctx, p, n, k, m, c, c, out, nullptr, ld_out, st, true, bias);
+}
+
+fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n, int k, int m,
+                                         const double* c_amp, const double* c_ph, float* im, float* re,
+                                         int64_t ld_out, cudaStream_t st, void* p_hi, void* p_lo, void* c_hi,
+                                         void* c_lo) {
+  if (k > 128) return fail(ctx, FKK_ERR_INVALID_ARG, "k > 128");
+  return recon_tc_run(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, st, p_hi, p_lo, c_hi, c_lo, false, nullptr);
 }
 
 }  // namespace fkk

@@ -38,7 +38,8 @@ def _params(fk, **kw):
     p = fk.fit_params(sec_mode=fk.SEC_SAVGOL if mode == "sg" else fk.SEC_MEAN, **kw)
     po = O.FitParams(pec=bool(p.pec), sec=bool(p.sec), als_lambda=(p.als_lambda or None), als_p=p.als_p,
                      als_iters=p.als_iters, sec_mode=mode, sg_window=p.sg_window, sg_order=p.sg_order,
-                     pad_len=p.pad_len, ratio_floor=p.ratio_floor)
+                     pad_len=p.pad_len, ratio_floor=p.ratio_floor, denoise_k=p.denoise_k, k_max=p.k_max,
+                     rank_eps=p.rank_eps)
     return p, po
 
 
@@ -164,3 +165,56 @@ def test_conventional_full_size_sampled_rows(fk, ctx):
     _, want = O.conventional(cube.i_cars[rows].astype(np.float64), cube.i_ref.astype(np.float64), po)
     assert np.all(np.isfinite(got))
     assert rel_l2(got, want) <= RTOL_L2
+
+
+# ---------------------------------------------------------------------------
+# The workflow's SVD denoising of the raw spectra (Fig. 1(a)): k is chosen
+# where the singular values have a clear gap (s_5 / s_6 = 2.2 and 3.0 on the
+# two cubes), so the kept subspace is well determined.
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("h,w,m,seed,k,pec", [(32, 40, 256, 3, 5, True), (48, 48, 200, 5, 5, False),
+                                              (48, 48, 200, 5, 1, False)])
+def test_conventional_denoise_matches_oracle(fk, ctx, h, w, m, seed, k, pec):
+    i, ref = _cube(h, w, m, seed)
+    p, po = _params(fk, denoise_k=k, pec=int(pec), sec=int(pec))
+    im, re = _gpu(fk, ctx, i, ref, p)
+    re_o, im_o = O.conventional(i.astype(np.float64), ref.astype(np.float64), po)
+    assert rel_l2(im, im_o) <= RTOL_L2
+    assert rel_l2(re, re_o) <= RTOL_L2
+    assert ctx.sync_status()[0] == 0
+
+
+def test_conventional_denoise_rank_rule_on_the_simulation(fk, ctx):
+    """The noiseless simulation-shaped cube: the rank rule keeps 3 singular
+    vectors of the raw spectra (s_3 = 3.3e-3 s_1 above the cutoff 5.4e-4 s_1,
+    s_4 = 2.2e-5 s_1 below it)."""
+    from paper_2005_07132_gb300.synth import make_sim_cube
+    cube = make_sim_cube(0.5)
+    i = cube.i_cars.astype(np.float64)
+    assert O.svd_denoise(i, -1)[1] == 3
+    p, po = _params(fk, denoise_k=-1, pec=0, sec=1, sec_mode="mean")
+    im, re = _gpu(fk, ctx, cube.i_cars, cube.i_ref, p)
+    re_o, im_o = O.conventional(i, cube.i_ref.astype(np.float64), po)
+    assert rel_l2(im, im_o) <= RTOL_L2
+    assert rel_l2(re, re_o) <= RTOL_L2
+
+
+def test_conventional_full_rank_denoise_changes_nothing(fk, ctx):
+    """k = M keeps every singular vector: X V V^T = X up to rounding."""
+    i, ref = _cube(16, 16, 64, 7)
+    p0, _ = _params(fk)
+    p1, _ = _params(fk, denoise_k=64)
+    im0, _ = _gpu(fk, ctx, i, ref, p0, re=False)
+    im1, _ = _gpu(fk, ctx, i, ref, p1, re=False)
+    assert rel_l2(im1, im0) <= 1e-5
+
+
+def test_conventional_denoise_rejects_bad_arguments(fk, ctx):
+    i, ref = _cube(16, 16, 64, 7)
+    for kw in (dict(denoise_k=81), dict(denoise_k=65), dict(denoise_k=-1, k_max=0), dict(denoise_k=-1, k_max=81),
+               dict(denoise_k=-1, rank_eps=-1.0)):
+        p, _ = _params(fk, **kw)
+        with pytest.raises(fk.FkkError):
+            _gpu(fk, ctx, i, ref, p, re=False)
