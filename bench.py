@@ -152,7 +152,7 @@ def source_hash(files):
 
 
 STAGE_KERNEL = {  # stage -> (kernel, sources, bound)
-    "transform": ("transform_kernel", ["fit_prep.cu", "common.cuh"], "hbm"),
+    "transform": ("transform_tma_kernel", ["fit_prep.cu", "tc.cuh", "common.cuh"], "hbm"),
     "gram": ("gram_tc_kernel", ["gram.cu", "tc.cuh", "common.cuh"], "tensor"),
     "eig": ("tridiag_kernel", ["tridiag.cu", "df64.cuh", "common.cuh"], "alu"),
     "project": ("project_tc_kernel", ["project_tc.cu", "tc.cuh", "common.cuh"], "hbm"),

@@ -1,11 +1,17 @@
 // Gram matrix of the transformed cube on the 5th-generation tensor cores.
 //
 // G_d = D^T D over all spectra, D = hi + lo (two bf16 terms), computed as
-// hi.hi + hi.lo + lo.hi + lo.lo with fp32 accumulation in TMEM: every
-// product of two bf16 values is exact in fp32, so the only error left is
-// the rounding of d to hi + lo (2^-18 |d|, unbiased) and the fp32
-// accumulation (kept short by the split-K).  Dropping lo.lo would leave a
-// systematic positive bias of ~2^-18 sum d^2 on the diagonal.  Output tiles are
+// hi.hi + hi.lo + lo.hi with fp32 accumulation in TMEM: every product of
+// two bf16 values is exact in fp32, so the errors left are the rounding of d
+// to hi + lo (2^-18 |d|, unbiased), the fp32 accumulation (kept short by the
+// split-K) and the dropped lo.lo term.  Off the diagonal, sum_n lo_i lo_j is a
+// sum of products of rounding residuals, 2^-16 below the other terms and of
+// either sign; on the diagonal it would be a positive bias of ~2^-18 sum d^2,
+// so the diagonal is taken instead from the exact sum_n d_j^2 of the
+// transform (fp32 within a 64-row tile, fp64 across tiles).  On the test
+// cubes this leaves the spectral-norm error of G where four products put it
+// (1e-7 of ||G||).  The rectangular A^T Q of the randomised SVD keeps all
+// four products.  Output tiles are
 // 128 (rows i) x 256 (columns j) covering the upper triangle (i-block 128*ib
 // < 256*(jb+1)); the contraction over spectra is split into `splits`
 // contiguous ranges, one CTA per (tile, split), and the fp32 partial tiles
@@ -167,7 +173,8 @@ __global__ void __launch_bounds__(128, 1)
                      (i > 0 || kk > 0) ? 1u : 0u);
         tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_hi + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
         tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_hi + off), idesc, 1u);
-        tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
+        if (RECT)
+          tc::mma_bf16(taddr, tc::sdesc_kmajor_sw128(a_lo + off), tc::sdesc_kmajor_sw128(b_lo + off), idesc, 1u);
       }
       tc::mma_commit(&empty[s]);
     }
@@ -209,7 +216,8 @@ __global__ void __launch_bounds__(128, 1)
 // f, write both triangles of the m x m matrix.
 __global__ void gram_assemble_kernel(const float* __restrict__ partial, int splits, int ntiles, int mb, int m,
                                      int64_t n, const float* __restrict__ c, const double* __restrict__ sd,
-                                     const double* __restrict__ f, double* __restrict__ g) {
+                                     const double* __restrict__ sd2, const double* __restrict__ f,
+                                     double* __restrict__ g) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
   if (j >= m || j < i) return;
@@ -220,7 +228,11 @@ __global__ void gram_assemble_kernel(const float* __restrict__ partial, int spli
   const int64_t off = ((int64_t)tile * kTileM + (i - ib * kTileM)) * kTileN + (j - jb * kTileN);
   const int64_t tstride = (int64_t)ntiles * kTileM * kTileN;
   double acc = 0.0;
-  for (int s = 0; s < splits; ++s) acc += (double)partial[s * tstride + off];
+  if (i == j) {
+    acc = sd2[i];  // exact sum of d^2 (the tiles lack lo.lo)
+  } else {
+    for (int s = 0; s < splits; ++s) acc += (double)partial[s * tstride + off];
+  }
   const double ci = c[i], cj = c[j];
   acc += sd[i] * cj + ci * sd[j] + (double)n * ci * cj;
   if (f) acc *= f[i] * f[j];
@@ -332,7 +344,8 @@ fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double*
   FKK_COUNT_LAUNCH(); kern<<<dim3(ntiles, (unsigned)splits), 128, gram_smem<kTileN>(), st>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
   FKK_CUDA(ctx, cudaGetLastError());
   dim3 grid((L.m + 127) / 128, L.m);
-  FKK_COUNT_LAUNCH(); gram_assemble_kernel<<<grid, 128, 0, st>>>(partial, (int)splits, ntiles, mb, L.m, L.n, L.c, L.sum_d, f, g);
+  FKK_COUNT_LAUNCH(); gram_assemble_kernel<<<grid, 128, 0, st>>>(partial, (int)splits, ntiles, mb, L.m, L.n, L.c, L.sum_d, L.sum_d2, f,
+                                                                 g);
   return cuda_check(ctx, cudaGetLastError(), "gram_assemble launch");
 }
 

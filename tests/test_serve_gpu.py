@@ -150,14 +150,15 @@ def test_serve_tune_cache_written(fk, ctx, trained, tmp_path):
 def test_serve_wait_timeout_then_complete(fk, ctx, trained):
     cube, x, ref, basis = trained
     srv = fk.Server(ctx, basis)
-    big = torch.cat([x] * 40).contiguous()  # ~123k spectra, several ms
-    out_big = torch.empty_like(big)
+    big = torch.cat([x] * 40).contiguous()  # ~123k spectra per tile
+    outs = [torch.empty_like(big) for _ in range(12)]
     small = x[:64].contiguous()
     out_small = torch.empty_like(small)
-    r1 = srv.submit(big, out_big)
-    r2 = srv.submit(small, out_small)  # queued behind the big tile
+    rs = [srv.submit(big, o) for o in outs]  # milliseconds of work queued ahead
+    r2 = srv.submit(small, out_small)
     assert srv.wait(r2, 0) == FKK_ERR_TIMEOUT
-    assert srv.wait(r1, -1) == 0
+    for r in rs:
+        assert srv.wait(r, -1) == 0
     assert srv.wait(r2, -1) == 0
     assert srv.wait(r2, 0) != 0  # released id
     srv.stop()
