@@ -25,6 +25,15 @@ fkk_status cuda_check(fkk_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, FKK_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+fkk_status side_stream(fkk_ctx* ctx, cudaStream_t* out) {
+  if (!ctx->aux) {
+    FKK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    FKK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    FKK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
+  *out = ctx->aux;
+  return FKK_OK;
+}
 fkk_status bind(fkk_ctx* ctx) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   return cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -117,6 +126,9 @@ fkk_status fkk_destroy(fkk_ctx* ctx) {
     if (kv.second.ptr) cudaFree(kv.second.ptr);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
   return FKK_OK;

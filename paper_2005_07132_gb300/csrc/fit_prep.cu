@@ -6,6 +6,7 @@
 //   sum_n a a^T = sum_n d d^T + s c^T + c s^T + N c c^T,  s = sum_n d,
 // while shrinking the magnitudes the tensor-core Gram accumulates.
 #include "common.cuh"
+#include "df64.cuh"
 #include "fit.h"
 #include "tc.cuh"
 
@@ -14,23 +15,37 @@ namespace {
 
 constexpr int kShiftRows = 256;
 
-__global__ void shift_kernel(const float* __restrict__ i_cars, int64_t n, int m, int64_t ld,
-                             const float* __restrict__ i_ref, float floor_, float* __restrict__ c, int raw) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  int rows = (int)(n < kShiftRows ? n : kShiftRows);
-  double acc = 0.0;
-  if (raw) {
-    for (int t = 0; t < rows; ++t) acc += i_cars[(int64_t)t * ld + j];
-  } else {
-    const float r = i_ref[j];
-    for (int t = 0; t < rows; ++t) {
-      float x = i_cars[(int64_t)t * ld + j] / r;
-      x = (x >= floor_) ? x : floor_;
-      acc += 0.5f * logf(x);
+// c[j] = mean over the first min(n, 256) rows of d (before the shift): a
+// block of 256 threads per 32 channels, each thread summing every 8th row of
+// one channel, the 8 partial sums combined in a fixed order.
+__global__ void __launch_bounds__(256) shift_kernel(const float* __restrict__ i_cars, int64_t n, int m, int64_t ld,
+                                                    const float* __restrict__ i_ref, float floor_,
+                                                    float* __restrict__ c, int raw) {
+  __shared__ float part[8][33];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const int rows = (int)(n < kShiftRows ? n : kShiftRows);
+  float acc = 0.f;
+  if (j < m) {
+    const float rinv = raw ? 1.f : 1.f / i_ref[j];
+    for (int t = g; t < rows; t += 8) {
+      const float v = i_cars[(int64_t)t * ld + j];
+      if (raw) {
+        acc += v;
+      } else {
+        float x = v * rinv;
+        x = (x >= floor_) ? x : floor_;
+        acc += 0.5f * logf(x);
+      }
     }
   }
-  c[j] = rows ? (float)(acc / rows) : 0.f;
+  part[g][lane] = acc;
+  __syncthreads();
+  if (g == 0 && j < m) {
+    float sum = 0.f;
+    for (int q = 0; q < 8; ++q) sum += part[q][lane];
+    c[j] = rows ? sum / (float)rows : 0.f;
+  }
 }
 
 // log2 by the SFU (PTX lg2.approx.f32, relative error near 2^-22): far below
@@ -192,7 +207,9 @@ __global__ void __launch_bounds__(256, 3)
     }
   }
   __syncthreads();
-  double sum_d = 0.0, sum_i = 0.0, sum_d2 = 0.0;
+  // per-thread channel sums in double-word arithmetic on the fp32 pipe (the
+  // fp64 pipe of this part would be a third busy with one add per tile)
+  dw::df sum_d = dw::make(0.f), sum_i = dw::make(0.f), sum_d2 = dw::make(0.f);
   int clamped = 0;
   int it = 0;
   for (int64_t rt = blockIdx.y; rt < nrt; rt += gstep, ++it) {
@@ -228,9 +245,9 @@ __global__ void __launch_bounds__(256, 3)
       ti += v;  // 0 outside the cube (TMA fill)
       tile[tx][r] = d;
     }
-    sum_d += td;
-    sum_d2 += td2;
-    sum_i += ti;
+    sum_d = dw::add(sum_d, td);
+    sum_d2 = dw::add(sum_d2, td2);
+    sum_i = dw::add(sum_i, ti);
     const int64_t rn = rt + (kTtStages - 1) * gstep;
     if (tid == 0 && rn < nrt) {
       // stage (it + 2) % 3 held tile it - 1: consumed, and its stores (issued
@@ -272,9 +289,9 @@ __global__ void __launch_bounds__(256, 3)
       record_error(p.status, kErrTimeout);
     }
   }
-  red_d[ty][tx] = sum_d;
-  red_d2[ty][tx] = sum_d2;
-  red_i[ty][tx] = sum_i;
+  red_d[ty][tx] = dw::to_double(sum_d);
+  red_d2[ty][tx] = dw::to_double(sum_d2);
+  red_i[ty][tx] = dw::to_double(sum_i);
   __syncthreads();
   if (ty == 0 && jvalid) {
     p.part_d[(int64_t)blockIdx.y * p.m + j] = red_d[0][tx] + red_d[1][tx] + red_d[2][tx] + red_d[3][tx];
@@ -338,7 +355,7 @@ fkk_status launch_transform(fkk_ctx* ctx, const float* i_cars, int64_t n, int m,
   if (!part_i) return s;
   double* part_d2 = (double*)workspace(ctx, "part_d2", (size_t)grows * m * 8, &s);
   if (!part_d2) return s;
-  FKK_COUNT_LAUNCH(); shift_kernel<<<(m + 127) / 128, 128, 0, st>>>(i_cars, n, m, ld, i_ref, floor_, L.c, raw ? 1 : 0);
+  FKK_COUNT_LAUNCH(); shift_kernel<<<(m + 31) / 32, 256, 0, st>>>(i_cars, n, m, ld, i_ref, floor_, L.c, raw ? 1 : 0);
   TransformArgs a{i_cars, n, m, ld, i_ref, floor_, L.c, L.np, L.dt_hi, L.dt_lo, part_d, part_i, part_d2, ctx->d_status};
   // TMA path: 16-byte aligned rows, at least one full tile each way
   if (tma_ok) {

@@ -38,6 +38,10 @@ struct fkk_ctx {
   static constexpr int kStages = 6;  // transform, gram, eig, project, basis, recon
   cudaEvent_t ev[kStages + 1] = {};
   bool ev_valid = false;
+  // side stream for work that overlaps the caller's stream inside one call
+  // (forked and joined with the two events; created on first use)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace fkk {
@@ -59,6 +63,9 @@ void* workspace(fkk_ctx* ctx, const char* name, size_t bytes, fkk_status* st);
 
 // Make the context's device current for this host thread.
 fkk_status bind(fkk_ctx* ctx);
+
+// The context's side stream (created on first use, with its fork / join events).
+fkk_status side_stream(fkk_ctx* ctx, cudaStream_t* out);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

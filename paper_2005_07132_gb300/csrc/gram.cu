@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "fit.h"
 #include "tc.cuh"
 
@@ -63,6 +64,7 @@ namespace {
 constexpr int kBK = 64;                       // spectra per K-block (128 bytes of bf16)
 constexpr int kTileM = 128, kTileN = 256;
 constexpr int kStages = 2;
+constexpr int kAccBlocks = 96;                // K-blocks per fp32 accumulation (6,144 spectra)
 constexpr uint32_t kABytes = kTileM * kBK * 2;  // 16 KB per term
 template <int TN>
 constexpr uint32_t stage_bytes() { return 2 * kABytes + 2 * (uint32_t)TN * kBK * 2; }
@@ -231,7 +233,17 @@ __global__ void gram_assemble_kernel(const float* __restrict__ partial, int spli
   if (i == j) {
     acc = sd2[i];  // exact sum of d^2 (the tiles lack lo.lo)
   } else {
-    for (int s = 0; s < splits; ++s) acc += (double)partial[s * tstride + off];
+    // the fp32 partials summed in double-word arithmetic on the fp32 pipe
+    // (about 48 bits; GB300's fp64 rate would make this the bottleneck):
+    // four chains for loads in flight, combined in a fixed order
+    dw::df a4[4] = {dw::make(0.f), dw::make(0.f), dw::make(0.f), dw::make(0.f)};
+    int s = 0;
+    for (; s + 4 <= splits; s += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a4[q] = dw::add(a4[q], partial[(int64_t)(s + q) * tstride + off]);
+    }
+    for (int q = 0; s < splits; ++s, ++q) a4[q] = dw::add(a4[q], partial[(int64_t)s * tstride + off]);
+    acc = dw::to_double(dw::add(dw::add(a4[0], a4[1]), dw::add(a4[2], a4[3])));
   }
   const double ci = c[i], cj = c[j];
   acc += sd[i] * cj + ci * sd[j] + (double)n * ci * cj;
@@ -268,8 +280,9 @@ __global__ void atq_assemble_kernel(const float* __restrict__ partial, int split
   const int ib = j / kTileM;
   const int64_t off = ((int64_t)ib * kTileM + (j - ib * kTileM)) * tn + i;
   const int64_t sstride = (int64_t)mb * kTileM * tn;
-  double acc = 0.0;
-  for (int s = 0; s < splits; ++s) acc += (double)partial[s * sstride + off];
+  dw::df a = dw::make(0.f);  // double-word sum on the fp32 pipe, in split order
+  for (int s = 0; s < splits; ++s) a = dw::add(a, partial[(int64_t)s * sstride + off]);
+  double acc = dw::to_double(a);
   acc += (double)c[j] * colsum[i];
   z[(int64_t)j * l + i] = f ? acc * f[j] : acc;
 }
@@ -281,7 +294,7 @@ fkk_status launch_atq(fkk_ctx* ctx, const DtLayout& L, const __nv_bfloat16* qt_h
   const int mb = L.mg / kTileM;
   const int64_t nkb = L.np / kBK;
   int64_t splits = ((int64_t)ctx->sm_count * 4 + mb - 1) / mb;
-  if (splits < (nkb + 95) / 96) splits = (nkb + 95) / 96;
+  if (splits < (nkb + kAccBlocks - 1) / kAccBlocks) splits = (nkb + kAccBlocks - 1) / kAccBlocks;
   if (splits > nkb) splits = nkb;
   if (splits < 1) splits = 1;
   float* partial = (float*)workspace(ctx, "atq_partial", (size_t)splits * mb * kTileM * tn * sizeof(float), &s);
@@ -319,10 +332,10 @@ fkk_status launch_gram(fkk_ctx* ctx, const DtLayout& L, const double* f, double*
   int ntiles = 0;
   for (int q = 0; q < jbs; ++q) ntiles += (2 * (q + 1) < mb ? 2 * (q + 1) : mb);
   const int64_t nkb = L.np / kBK;
-  // enough CTAs for several waves, at least 8 and at most 96 K-blocks each
-  // (the fp32 TMEM accumulation length per partial tile)
+  // enough CTAs for several waves, at least 8 and at most kAccBlocks
+  // K-blocks each (the fp32 TMEM accumulation length per partial tile)
   int64_t splits = ((int64_t)ctx->sm_count * 5 + ntiles - 1) / ntiles;
-  if (splits < (nkb + 95) / 96) splits = (nkb + 95) / 96;
+  if (splits < (nkb + kAccBlocks - 1) / kAccBlocks) splits = (nkb + kAccBlocks - 1) / kAccBlocks;
   if (splits > nkb / 8) splits = nkb / 8;
   if (splits < 1) splits = 1;
   float* partial =

@@ -226,18 +226,29 @@ __global__ void __launch_bounds__(kRecThreads, 1)
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
 }
 
-// P (n x k fp32) -> hi / lo bf16 (n_pad x kp, zero padded)
-__global__ void pack_p_kernel(const float* __restrict__ p, int64_t n, int k, int64_t n_pad, int kp,
+// P (n x k fp32) -> hi / lo bf16 (n_pad x kp, zero padded).  One thread per
+// 8 columns of a row (kp / 8 = 1 << g_shift groups per row): 16-byte stores
+// of each term.
+__global__ void pack_p_kernel(const float* __restrict__ p, int64_t n, int k, int64_t n_pad, int kp, int g_shift,
                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_pad * kp) return;
-  const int64_t r = t / kp;
-  const int c = (int)(t - r * kp);
-  const float v = (r < n && c < k) ? p[r * k + c] : 0.f;
-  __nv_bfloat16 h, l;
-  split_bf16(v, h, l);
-  hi[t] = h;
-  lo[t] = l;
+  if (t >= (n_pad * kp) >> 3) return;
+  const int64_t r = t >> g_shift;
+  const int c0 = (int)(t - (r << g_shift)) * 8;
+  float v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = (r < n && c0 + q < k) ? p[r * k + c0 + q] : 0.f;
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+    h[q] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[q] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  *reinterpret_cast<uint4*>(hi + r * kp + c0) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + r * kp + c0) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // C (k x m fp64 amp and phase) -> interleaved rows (2m_pad x kp): row 2j = amp
@@ -273,9 +284,9 @@ fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, c
   __nv_bfloat16* chi = static_cast<__nv_bfloat16*>(c_hi);
   __nv_bfloat16* clo = static_cast<__nv_bfloat16*>(c_lo);
   {
-    const int64_t tot = n_pad * kp;
+    const int64_t tot = (n_pad * kp) >> 3;  // 8 columns per thread
     FKK_COUNT_LAUNCH();
-    pack_p_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p, n, k, n_pad, kp, phi, plo);
+    pack_p_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p, n, k, n_pad, kp, kp == 64 ? 3 : 4, phi, plo);
     const int64_t totc = (int64_t)rows_c * kp;
     FKK_COUNT_LAUNCH();
     pack_c_kernel<<<(unsigned)((totc + 255) / 256), 256, 0, st>>>(c_amp, c_ph, k, m, rows_c, kp, chi, clo);

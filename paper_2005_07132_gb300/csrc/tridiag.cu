@@ -1267,6 +1267,27 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
     FKK_COUNT_LAUNCH();
     FKK_CUDA(ctx, cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kTrThreads), args, smem_tr, st));
   }
+  // 4a. the WY block factors of the reflectors depend on nothing else, so
+  // they run on the context's side stream beside steps 2-3
+  const int nrefl = std::max(0, m - 2);
+  df* tblk = nullptr;
+  if (nrefl > 0) {
+    const int nbk = (nrefl + kWY - 1) / kWY;
+    const int S = std::max(1, std::min(8, nsm / nbk));
+    df* gpart = (df*)workspace(ctx, "tri_gpart", (size_t)nbk * S * kWY * kWY * sizeof(df), &s);
+    if (!gpart) return s;
+    tblk = (df*)workspace(ctx, "tri_tblk", (size_t)nbk * kWY * kWY * sizeof(df), &s);
+    if (!tblk) return s;
+    cudaStream_t aux = nullptr;
+    FKK_TRY(side_stream(ctx, &aux));
+    FKK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
+    FKK_CUDA(ctx, cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
+    FKK_COUNT_LAUNCH();
+    wy_gram_kernel<<<dim3(nbk, S), kWyThreads, 0, aux>>>(u, m, nrefl, S, gpart);
+    FKK_COUNT_LAUNCH();
+    wy_t_kernel<<<nbk, 32, 0, aux>>>(gpart, tau, nrefl, S, tblk);
+    FKK_CUDA(ctx, cudaEventRecord(ctx->ev_join, aux));
+  }
   // 2-3. eigenvalues and tridiagonal eigenvectors
   df* z = (df*)workspace(ctx, "tri_z", (size_t)m * k * sizeof(df), &s);
   if (!z) return s;
@@ -1285,19 +1306,9 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
     lam_out_kernel<<<(k + 127) / 128, 128, 0, st>>>(lam_s, ex_dev, k, lam);
     FKK_CUDA(ctx, cudaGetLastError());
   }
-  // 4. back-transformation
-  const int nrefl = std::max(0, m - 2);
+  // 4b. back-transformation of the eigenvectors
   if (nrefl > 0) {
-    const int nbk = (nrefl + kWY - 1) / kWY;
-    const int S = std::max(1, std::min(8, nsm / nbk));
-    df* gpart = (df*)workspace(ctx, "tri_gpart", (size_t)nbk * S * kWY * kWY * sizeof(df), &s);
-    if (!gpart) return s;
-    df* tblk = (df*)workspace(ctx, "tri_tblk", (size_t)nbk * kWY * kWY * sizeof(df), &s);
-    if (!tblk) return s;
-    FKK_COUNT_LAUNCH();
-    wy_gram_kernel<<<dim3(nbk, S), kWyThreads, 0, st>>>(u, m, nrefl, S, gpart);
-    FKK_COUNT_LAUNCH();
-    wy_t_kernel<<<nbk, 32, 0, st>>>(gpart, tau, nrefl, S, tblk);
+    FKK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
     const size_t sa = ((size_t)2 * m + kWY * kWY + 4 * kWY) * sizeof(df);
     FKK_CUDA(ctx, cudaFuncSetAttribute(wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
     FKK_COUNT_LAUNCH();
