@@ -120,4 +120,45 @@ __device__ __forceinline__ df warp_sum(df x) {
 }
 
 }  // namespace dw
+
+// Two independent double-word numbers carried side by side, (h.x, l.x) and
+// (h.y, l.y), on Blackwell's paired fp32 instructions.  Every operation is
+// dw's with the same rounding per component (the paired instructions round
+// each lane as their scalar _rn forms do), so the results are bit-identical
+// to two dw computations, in about half the instructions.
+namespace dw2 {
+
+struct df2 {
+  float2 h, l;
+};
+
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ df2 pack(dw::df a, dw::df b) { return {make_float2(a.h, b.h), make_float2(a.l, b.l)}; }
+__device__ __forceinline__ df2 splat(dw::df a) { return {make_float2(a.h, a.h), make_float2(a.l, a.l)}; }
+
+__device__ __forceinline__ df2 two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = __fadd2_rn(s, neg(a));
+  const float2 e = __fadd2_rn(__fadd2_rn(a, neg(__fadd2_rn(s, neg(bb)))), __fadd2_rn(b, neg(bb)));
+  return {s, e};
+}
+__device__ __forceinline__ df2 fast_two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 e = __fadd2_rn(b, neg(__fadd2_rn(s, neg(a))));
+  return {s, e};
+}
+__device__ __forceinline__ df2 add(df2 x, df2 y) {
+  const df2 s = two_sum(x.h, y.h);
+  const float2 t = __fadd2_rn(__fadd2_rn(x.l, y.l), s.l);
+  return fast_two_sum(s.h, t);
+}
+__device__ __forceinline__ df2 sub(df2 x, df2 y) { return add(x, {neg(y.h), neg(y.l)}); }
+__device__ __forceinline__ df2 mul(df2 x, df2 y) {
+  const float2 p = __fmul2_rn(x.h, y.h);
+  const float2 pe = __ffma2_rn(x.h, y.h, neg(p));
+  const float2 t = __ffma2_rn(x.l, y.h, __fmul2_rn(x.h, y.l));
+  return fast_two_sum(p, __fadd2_rn(pe, t));
+}
+
+}  // namespace dw2
 }  // namespace fkk

@@ -532,75 +532,66 @@ __device__ __forceinline__ float rescale_factor(float a, float b) {
 // to the largest diagonal entry at every step, so the pair is rescaled by a
 // power of two whenever the larger leaves [2^-32, 2^32]: the float exponent
 // of a double-word would otherwise underflow within a few steps.
-__device__ __forceinline__ int sturm_count(const df* ds, const df* eb, int m, df x) {
-  df p2 = dw::make(1.f);
-  df p1 = dw::sub(ds[0], x);
-  if (p1.h == 0.f) p1 = dw::make(-0x1p-60f);
-  int cnt = p1.h < 0.f;
-  for (int i = 1; i < m; ++i) {
-    df p = dw::sub(dw::mul(dw::sub(ds[i], x), p1), dw::mul(eb[i], p2));
-    if (p.h == 0.f) p = dw::mul(p1, -0x1p-60f);
-    cnt += (p.h < 0.f) != (p1.h < 0.f);
-    p2 = p1;
-    p1 = p;
-    const float f = rescale_factor(p1.h, p2.h);
-    if (f != 1.f) {
-      p1 = dw::mul(p1, f);
-      p2 = dw::mul(p2, f);
-    }
-  }
-  return cnt;
-}
-
-// Two counts at once (independent recurrences interleaved, to hide the
-// dependent latency of each).
+// Two counts at once: the two recurrences run side by side on the paired
+// fp32 instructions (dw2), which also hides the dependent latency of each.
+// Bit-identical to two separate double-word counts.
 __device__ __forceinline__ void sturm_count2(const df* ds, const df* eb, int m, df x, df y, int& nx, int& ny) {
-  df p2 = dw::make(1.f), q2 = p2;
-  df p1 = dw::sub(ds[0], x), q1 = dw::sub(ds[0], y);
-  if (p1.h == 0.f) p1 = dw::make(-0x1p-60f);
-  if (q1.h == 0.f) q1 = dw::make(-0x1p-60f);
-  int cx = p1.h < 0.f, cy = q1.h < 0.f;
+  const dw2::df2 xy = dw2::pack(x, y);
+  dw2::df2 pq2 = dw2::pack(dw::make(1.f), dw::make(1.f));
+  dw2::df2 pq1 = dw2::sub(dw2::splat(ds[0]), xy);
+  if (pq1.h.x == 0.f) {
+    pq1.h.x = -0x1p-60f;
+    pq1.l.x = 0.f;
+  }
+  if (pq1.h.y == 0.f) {
+    pq1.h.y = -0x1p-60f;
+    pq1.l.y = 0.f;
+  }
+  int cx = pq1.h.x < 0.f, cy = pq1.h.y < 0.f;
   for (int i = 1; i < m; ++i) {
-    const df di = ds[i], ei = eb[i];
-    df p = dw::sub(dw::mul(dw::sub(di, x), p1), dw::mul(ei, p2));
-    df q = dw::sub(dw::mul(dw::sub(di, y), q1), dw::mul(ei, q2));
+    const dw2::df2 d2 = dw2::splat(ds[i]), e2 = dw2::splat(eb[i]);
+    dw2::df2 pq = dw2::sub(dw2::mul(dw2::sub(d2, xy), pq1), dw2::mul(e2, pq2));
     // branch-free: an exact zero becomes a tiny negative multiple of the
     // previous minor; the rescale factor is 1 when none is needed (exact)
-    const bool pz = p.h == 0.f, qz = q.h == 0.f;
-    p.h = pz ? -0x1p-60f * p1.h : p.h;
-    p.l = pz ? 0.f : p.l;
-    q.h = qz ? -0x1p-60f * q1.h : q.h;
-    q.l = qz ? 0.f : q.l;
-    cx += (p.h < 0.f) != (p1.h < 0.f);
-    cy += (q.h < 0.f) != (q1.h < 0.f);
-    const float f = rescale_factor(p.h, p1.h), g = rescale_factor(q.h, q1.h);
-    p2 = {p1.h * f, p1.l * f};
-    p1 = {p.h * f, p.l * f};
-    q2 = {q1.h * g, q1.l * g};
-    q1 = {q.h * g, q.l * g};
+    const bool pz = pq.h.x == 0.f, qz = pq.h.y == 0.f;
+    pq.h.x = pz ? -0x1p-60f * pq1.h.x : pq.h.x;
+    pq.l.x = pz ? 0.f : pq.l.x;
+    pq.h.y = qz ? -0x1p-60f * pq1.h.y : pq.h.y;
+    pq.l.y = qz ? 0.f : pq.l.y;
+    cx += (pq.h.x < 0.f) != (pq1.h.x < 0.f);
+    cy += (pq.h.y < 0.f) != (pq1.h.y < 0.f);
+    const float2 fg = make_float2(rescale_factor(pq.h.x, pq1.h.x), rescale_factor(pq.h.y, pq1.h.y));
+    pq2 = {__fmul2_rn(pq1.h, fg), __fmul2_rn(pq1.l, fg)};
+    pq1 = {__fmul2_rn(pq.h, fg), __fmul2_rn(pq.l, fg)};
   }
   nx = cx;
   ny = cy;
 }
 
-// The same count in plain fp32 on the leading words: exact for a matrix
-// within a few float roundings of Ts, used to bracket before the
+// The same pair of counts in plain fp32 on the leading words: exact for a
+// matrix within a few float roundings of Ts, used to bracket before the
 // double-word rounds.
-__device__ __forceinline__ int sturm_count_f32(const df* ds, const df* eb, int m, float x) {
-  float p2 = 1.f, p1 = ds[0].h - x;
-  if (p1 == 0.f) p1 = -0x1p-60f;
-  int cnt = p1 < 0.f;
+__device__ __forceinline__ void sturm_count2_f32(const df* ds, const df* eb, int m, float x, float y, int& nx,
+                                                 int& ny) {
+  const float2 nxy = make_float2(-x, -y);
+  float2 p2 = make_float2(1.f, 1.f);
+  float2 p1 = __fadd2_rn(make_float2(ds[0].h, ds[0].h), nxy);
+  if (p1.x == 0.f) p1.x = -0x1p-60f;
+  if (p1.y == 0.f) p1.y = -0x1p-60f;
+  int cx = p1.x < 0.f, cy = p1.y < 0.f;
   for (int i = 1; i < m; ++i) {
-    float p = fmaf(ds[i].h - x, p1, -eb[i].h * p2);
-    if (p == 0.f) p = -0x1p-60f * p1;
-    cnt += (p < 0.f) != (p1 < 0.f);
-    p2 = p1;
-    p1 = p;
-    const float f = rescale_factor(p1, p2);
-    p1 *= f;
-    p2 *= f;
+    const float d = ds[i].h, e = eb[i].h;
+    float2 p = __ffma2_rn(__fadd2_rn(make_float2(d, d), nxy), p1, __fmul2_rn(make_float2(-e, -e), p2));
+    if (p.x == 0.f) p.x = -0x1p-60f * p1.x;
+    if (p.y == 0.f) p.y = -0x1p-60f * p1.y;
+    cx += (p.x < 0.f) != (p1.x < 0.f);
+    cy += (p.y < 0.f) != (p1.y < 0.f);
+    const float2 fg = make_float2(rescale_factor(p.x, p1.x), rescale_factor(p.y, p1.y));
+    p2 = __fmul2_rn(p1, fg);
+    p1 = __fmul2_rn(p, fg);
   }
-  return cnt;
+  nx = cx;
+  ny = cy;
 }
 
 // First of the 2 x blockDim points (thread t holds points 2t and 2t + 1)
@@ -657,7 +648,8 @@ __global__ void __launch_bounds__(kBisWarps * 32) tri_bisect_kernel(const df* __
   for (int round = 0; round < 8 && fhi - flo > 64.f * kEpsF * gmax; ++round) {
     const float x0 = flo + (fhi - flo) * ((float)(2 * tid + 1) / (float)(P + 1));
     const float x1 = flo + (fhi - flo) * ((float)(2 * tid + 2) / (float)(P + 1));
-    const int n0 = sturm_count_f32(ds, eb, m, x0), n1 = sturm_count_f32(ds, eb, m, x1);
+    int n0, n1;
+    sturm_count2_f32(ds, eb, m, x0, x1, n0, n1);
     const int first = first_above2(n0, n1, r, first_s);
     if (first - 1 == 2 * tid) flh[0] = x0;
     if (first - 1 == 2 * tid + 1) flh[0] = x1;
@@ -962,35 +954,31 @@ __global__ void __launch_bounds__(32) wy_t_kernel(const df* __restrict__ gpart, 
 // carries four independent double-word accumulations (two reflectors or
 // two rows, times two columns) to hide their dependent latency.
 constexpr int kApThreads = 512;
-__global__ void __launch_bounds__(kApThreads) wy_apply_kernel(const df* __restrict__ u, const df* __restrict__ tblk,
+__global__ void __launch_bounds__(kApThreads, 1) wy_apply_kernel(const df* __restrict__ u, const df* __restrict__ tblk,
                                                               int m, int nrefl, int k, const df* __restrict__ z,
                                                               double* __restrict__ v) {
   extern __shared__ df smd[];
-  df* z0 = smd;               // [m]
-  df* z1 = z0 + m;            // [m]
-  df* ts = z1 + m;            // [32 x 32]
-  df* wv = ts + kWY * kWY;    // [2][32]
-  df* tv = wv + 2 * kWY;      // [2][32]
+  df* zc = smd;            // [m] this CTA's column
+  df* ts = zc + m;         // [32 x 32]
+  df* wv = ts + kWY * kWY; // [32]
+  df* tv = wv + kWY;       // [32]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kWarps = kApThreads / 32;
-  const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
-  const bool has1 = c1 < k;
-  for (int i = tid; i < m; i += kApThreads) {
-    z0[i] = z[(size_t)i * k + c0];
-    z1[i] = has1 ? z[(size_t)i * k + c1] : dw::make(0.f);
-  }
+  const int c = blockIdx.x;
+  for (int i = tid; i < m; i += kApThreads) zc[i] = z[(size_t)i * k + c];
   __syncthreads();  // every warp reads rows other warps loaded
   const int nbk = (nrefl + kWY - 1) / kWY;
   for (int b = nbk - 1; b >= 0; --b) {
     const int j0 = b * kWY, nr = min(kWY, nrefl - j0);
     for (int x = tid; x < kWY * kWY; x += kApThreads) ts[x] = tblk[(size_t)b * kWY * kWY + x];
-    // w = Y^T z over rows >= j0 + 1: warp takes reflectors warp and warp + 16
+    // w = Y^T z over rows >= j0 + 1: warp takes reflectors warp and warp + 16,
+    // the two sums side by side (dw2)
     {
       const int pa = warp, pb = warp + kWarps;
       const df* ya = u + (size_t)(j0 + pa) * m;
       const df* yb = u + (size_t)(j0 + pb) * m;
       const bool va = pa < nr, vb = pb < nr;
-      df a0 = dw::make(0.f), a1 = a0, b0 = a0, b1 = a0;
+      dw2::df2 acc = dw2::pack(dw::make(0.f), dw::make(0.f));
       // four rows per lane per iteration, their loads issued together
       for (int i = j0 + 1 + lane; i < m; i += 128) {
         df ra[4], rb[4];
@@ -1004,38 +992,30 @@ __global__ void __launch_bounds__(kApThreads) wy_apply_kernel(const df* __restri
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int ii = i + 32 * t;
-          if (ii < m) {
-            const df zi0 = z0[ii], zi1 = z1[ii];
-            a0 = dw::add(a0, dw::mul(ra[t], zi0));
-            a1 = dw::add(a1, dw::mul(ra[t], zi1));
-            b0 = dw::add(b0, dw::mul(rb[t], zi0));
-            b1 = dw::add(b1, dw::mul(rb[t], zi1));
-          }
+          if (ii < m) acc = dw2::add(acc, dw2::mul(dw2::pack(ra[t], rb[t]), dw2::splat(zc[ii])));
         }
       }
-      a0 = dw::warp_sum(a0);
-      a1 = dw::warp_sum(a1);
-      b0 = dw::warp_sum(b0);
-      b1 = dw::warp_sum(b1);
+      const df a0 = dw::warp_sum(dw::make(acc.h.x, acc.l.x));
+      const df b0 = dw::warp_sum(dw::make(acc.h.y, acc.l.y));
       if (lane == 0) {
-        if (va) { wv[pa] = a0; wv[kWY + pa] = a1; }
-        if (vb) { wv[pb] = b0; wv[kWY + pb] = b1; }
+        if (va) wv[pa] = a0;
+        if (vb) wv[pb] = b0;
       }
     }
     __syncthreads();
-    // t = T w (upper triangular), both columns
-    if (warp < 2) {
+    // t = T w (upper triangular)
+    if (warp == 0) {
       df acc = dw::make(0.f);
       if (lane < nr)
-        for (int q = lane; q < nr; ++q) acc = dw::add(acc, dw::mul(ts[lane * kWY + q], wv[warp * kWY + q]));
-      tv[warp * kWY + lane] = acc;
+        for (int q = lane; q < nr; ++q) acc = dw::add(acc, dw::mul(ts[lane * kWY + q], wv[q]));
+      tv[lane] = acc;
     }
     __syncthreads();
-    // z -= Y t: thread takes rows i and i + kApThreads
+    // z -= Y t: thread takes rows i and i + kApThreads, side by side (dw2)
     for (int i = j0 + 1 + tid; i < m; i += 2 * kApThreads) {
       const int i2 = i + kApThreads;
       const bool v2 = i2 < m;
-      df s0 = dw::make(0.f), s1 = s0, r0 = s0, r1 = s0;
+      dw2::df2 sr = dw2::pack(dw::make(0.f), dw::make(0.f));
       // eight reflectors per iteration, their loads issued together
       for (int p0 = 0; p0 < nr; p0 += 8) {
         df ya[8], yb[8];
@@ -1049,28 +1029,15 @@ __global__ void __launch_bounds__(kApThreads) wy_apply_kernel(const df* __restri
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int pr = p0 + t;
-          if (pr < nr) {
-            const df t0 = tv[pr], t1 = tv[kWY + pr];
-            s0 = dw::add(s0, dw::mul(ya[t], t0));
-            s1 = dw::add(s1, dw::mul(ya[t], t1));
-            r0 = dw::add(r0, dw::mul(yb[t], t0));
-            r1 = dw::add(r1, dw::mul(yb[t], t1));
-          }
+          if (pr < nr) sr = dw2::add(sr, dw2::mul(dw2::pack(ya[t], yb[t]), dw2::splat(tv[pr])));
         }
       }
-      z0[i] = dw::sub(z0[i], s0);
-      z1[i] = dw::sub(z1[i], s1);
-      if (v2) {
-        z0[i2] = dw::sub(z0[i2], r0);
-        z1[i2] = dw::sub(z1[i2], r1);
-      }
+      zc[i] = dw::sub(zc[i], dw::make(sr.h.x, sr.l.x));
+      if (v2) zc[i2] = dw::sub(zc[i2], dw::make(sr.h.y, sr.l.y));
     }
     __syncthreads();
   }
-  for (int i = tid; i < m; i += kApThreads) {
-    v[(size_t)i * k + c0] = dw::to_double(z0[i]);
-    if (has1) v[(size_t)i * k + c1] = dw::to_double(z1[i]);
-  }
+  for (int i = tid; i < m; i += kApThreads) v[(size_t)i * k + c] = dw::to_double(zc[i]);
 }
 
 // Z (double-word) to fp64, for m <= 2 (no reflectors).
@@ -1309,10 +1276,10 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
   // 4b. back-transformation of the eigenvectors
   if (nrefl > 0) {
     FKK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
-    const size_t sa = ((size_t)2 * m + kWY * kWY + 4 * kWY) * sizeof(df);
+    const size_t sa = ((size_t)m + kWY * kWY + 2 * kWY) * sizeof(df);
     FKK_CUDA(ctx, cudaFuncSetAttribute(wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
     FKK_COUNT_LAUNCH();
-    wy_apply_kernel<<<(k + 1) / 2, kApThreads, sa, st>>>(u, tblk, m, nrefl, k, z, vz);
+    wy_apply_kernel<<<k, kApThreads, sa, st>>>(u, tblk, m, nrefl, k, z, vz);
     FKK_CUDA(ctx, cudaGetLastError());
   } else {
     FKK_COUNT_LAUNCH();
