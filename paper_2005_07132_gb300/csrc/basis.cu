@@ -14,6 +14,8 @@
 namespace fkk {
 namespace {
 
+using dw::df;
+
 // ------------------------------------------------------------------ q ---
 __global__ void gather_q_kernel(const int64_t* __restrict__ qmax, const int64_t* __restrict__ qmin, int k,
                                 int64_t n_rows, int64_t* __restrict__ q, int* __restrict__ nq, long long* status) {
@@ -112,70 +114,89 @@ __global__ void small_gemm_kernel(const double* __restrict__ X, const double* __
 // ---------------------------------------------------------------- ALS ---
 // Asymmetric least squares baseline of one row per block: repeat `iters`
 // times: solve (W + lam D2^T D2) z = W y, then w_i = p if y_i > z_i else
-// 1 - p (weights start at 1).  The pentadiagonal SPD system is solved in
-// fp64 as a block-tridiagonal system of 2 x 2 blocks (unknown pairs
-// (z_2i, z_2i+1)) by cyclic reduction: log2(P) levels of elimination and
-// back-substitution with the block rows of each level in parallel.  P is
-// the block count padded to a power of two with identity rows.
+// 1 - p (weights start at 1).  The pentadiagonal SPD system is solved as a
+// block-tridiagonal system of 2 x 2 blocks (unknown pairs (z_2i, z_2i+1))
+// by cyclic reduction: log2(P) levels of elimination and back-substitution
+// with the block rows of each level in parallel.  P is the block count
+// padded to a power of two with identity rows.  The arithmetic is
+// double-word on the fp32 pipe (about 48 bits): the reduction's first
+// levels are ~10^5 operations per row, which this part's fp64 rate (about
+// 1.7 lane-operations per clock per SM) would make the bottleneck.
 
 // Band entries of D2^T D2 (D2 = (M-2) x M second differences): diagonal at j
 // and first off-diagonal (j, j+1); the second off-diagonal is 1 throughout.
-__device__ __forceinline__ double band0(int j, int m) {
-  double s = 0.0;
-  if (j <= m - 3) s += 1.0;
-  if (j >= 1 && j - 1 <= m - 3) s += 4.0;
-  if (j >= 2 && j - 2 <= m - 3) s += 1.0;
+__device__ __forceinline__ float band0(int j, int m) {
+  float s = 0.f;
+  if (j <= m - 3) s += 1.f;
+  if (j >= 1 && j - 1 <= m - 3) s += 4.f;
+  if (j >= 2 && j - 2 <= m - 3) s += 1.f;
   return s;
 }
-__device__ __forceinline__ double band1(int j, int m) {
-  double s = 0.0;
-  if (j >= 0 && j <= m - 3) s += -2.0;
-  if (j >= 1 && j - 1 <= m - 3) s += -2.0;
+__device__ __forceinline__ float band1(int j, int m) {
+  float s = 0.f;
+  if (j >= 0 && j <= m - 3) s += -2.f;
+  if (j >= 1 && j - 1 <= m - 3) s += -2.f;
   return s;
 }
 
 struct Blk {
-  double a, b, c, d;  // [[a, b], [c, d]]
+  df a, b, c, d;  // [[a, b], [c, d]]
 };
+struct Vec2 {
+  df x, y;
+};
+__device__ __forceinline__ df dot2(df p, df q, df r, df t) { return dw::add(dw::mul(p, q), dw::mul(r, t)); }
 __device__ __forceinline__ Blk bmul(const Blk& x, const Blk& y) {
-  return {fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c), fma(x.c, y.b, x.d * y.d)};
+  return {dot2(x.a, y.a, x.b, y.c), dot2(x.a, y.b, x.b, y.d), dot2(x.c, y.a, x.d, y.c), dot2(x.c, y.b, x.d, y.d)};
 }
+__device__ __forceinline__ Blk badd(const Blk& x, const Blk& y) {
+  return {dw::add(x.a, y.a), dw::add(x.b, y.b), dw::add(x.c, y.c), dw::add(x.d, y.d)};
+}
+__device__ __forceinline__ Blk bneg(const Blk& x) { return {dw::neg(x.a), dw::neg(x.b), dw::neg(x.c), dw::neg(x.d)}; }
 __device__ __forceinline__ Blk binv(const Blk& x) {
-  double det = fma(x.a, x.d, -x.b * x.c);
-  double r = 1.0 / det;
-  return {x.d * r, -x.b * r, -x.c * r, x.a * r};
+  const df det = dw::sub(dw::mul(x.a, x.d), dw::mul(x.b, x.c));
+  const df r = dw::rcp(det);
+  return {dw::mul(x.d, r), dw::neg(dw::mul(x.b, r)), dw::neg(dw::mul(x.c, r)), dw::mul(x.a, r)};
 }
-__device__ __forceinline__ double2 bvec(const Blk& x, double2 v) {
-  return make_double2(fma(x.a, v.x, x.b * v.y), fma(x.c, v.x, x.d * v.y));
+__device__ __forceinline__ Vec2 bvec(const Blk& x, const Vec2& v) {
+  return {dot2(x.a, v.x, x.b, v.y), dot2(x.c, v.x, x.d, v.y)};
 }
+__device__ __forceinline__ Vec2 vadd(const Vec2& u, const Vec2& v) { return {dw::add(u.x, v.x), dw::add(u.y, v.y)}; }
+__device__ __forceinline__ Vec2 vsub(const Vec2& u, const Vec2& v) { return {dw::sub(u.x, v.x), dw::sub(u.y, v.y)}; }
+// u > v for normalised double-words
+__device__ __forceinline__ bool dgt(df u, df v) { return u.h > v.h || (u.h == v.h && u.l > v.l); }
 
-__global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_all, int m, int P, double lam, double p,
-                                                  int iters, double* __restrict__ z_all, const int* __restrict__ rows_dev) {
+__global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_all, int m, int P, double lam_d,
+                                                  double p_d, int iters, double* __restrict__ z_all,
+                                                  const int* __restrict__ rows_dev) {
   extern __shared__ double als_sm[];
   const int row = blockIdx.x;
   if (rows_dev && row >= *rows_dev) return;
   Blk* A = reinterpret_cast<Blk*>(als_sm);
   Blk* B = A + P;
   Blk* C = B + P;
-  double2* D = reinterpret_cast<double2*>(C + P);
-  double* y = reinterpret_cast<double*>(D + P);
-  double* w = y + 2 * P;
-  double* z = w + 2 * P;
+  Vec2* D = reinterpret_cast<Vec2*>(C + P);
+  df* y = reinterpret_cast<df*>(D + P);
+  df* w = y + 2 * P;
+  df* z = w + 2 * P;
   const double* yr = y_all + (int64_t)row * m;
+  const df lam = dw::from_double(lam_d);
+  const df wp = dw::from_double(p_d), wq = dw::from_double(1.0 - p_d);
+  const df one = dw::make(1.f), zero = dw::make(0.f);
   for (int j = threadIdx.x; j < 2 * P; j += blockDim.x) {
-    y[j] = j < m ? yr[j] : 0.0;
-    w[j] = 1.0;
+    y[j] = j < m ? dw::from_double(yr[j]) : zero;
+    w[j] = one;
   }
   __syncthreads();
   // matrix entry a(j, l) for |j - l| <= 2 (identity outside the signal)
-  auto ent = [&](int j, int l) -> double {
-    if (j < 0 || l < 0 || j >= 2 * P || l >= 2 * P) return 0.0;
-    if (j >= m || l >= m) return (j == l) ? 1.0 : 0.0;
-    int d = j - l;
-    if (d == 0) return w[j] + lam * band0(j, m);
-    if (d == 1 || d == -1) return lam * band1(min(j, l), m);
+  auto ent = [&](int j, int l) -> df {
+    if (j < 0 || l < 0 || j >= 2 * P || l >= 2 * P) return zero;
+    if (j >= m || l >= m) return (j == l) ? one : zero;
+    const int d = j - l;
+    if (d == 0) return dw::add(w[j], dw::mul(lam, band0(j, m)));
+    if (d == 1 || d == -1) return dw::mul(lam, band1(min(j, l), m));
     if (d == 2 || d == -2) return lam;
-    return 0.0;
+    return zero;
   };
   for (int it = 0; it < iters; ++it) {
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_a
       B[i] = {ent(r0, r0), ent(r0, r1), ent(r1, r0), ent(r1, r1)};
       A[i] = {ent(r0, r0 - 2), ent(r0, r0 - 1), ent(r1, r0 - 2), ent(r1, r0 - 1)};
       C[i] = {ent(r0, r1 + 1), ent(r0, r1 + 2), ent(r1, r1 + 1), ent(r1, r1 + 2)};
-      D[i] = make_double2(r0 < m ? w[r0] * y[r0] : 0.0, r1 < m ? w[r1] * y[r1] : 0.0);
+      D[i] = {r0 < m ? dw::mul(w[r0], y[r0]) : zero, r1 < m ? dw::mul(w[r1], y[r1]) : zero};
     }
     __syncthreads();
     // forward reduction
@@ -192,30 +213,15 @@ __global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_a
         const int i = 2 * s * t + 2 * s - 1;
         const int im = i - s, ip = i + s;
         // alpha = -A_i B_im^-1, gamma = -C_i B_ip^-1
-        Blk ai = A[i], ci = C[i];
-        Blk bim_inv = binv(B[im]);
-        Blk alpha = bmul(ai, bim_inv);
-        alpha = {-alpha.a, -alpha.b, -alpha.c, -alpha.d};
-        Blk gamma = {0, 0, 0, 0};
+        const Blk alpha = bneg(bmul(A[i], binv(B[im])));
+        Blk nb = badd(B[i], bmul(alpha, C[im]));
+        Vec2 nd = vadd(D[i], bvec(alpha, D[im]));
+        const Blk na = bmul(alpha, A[im]);
+        Blk nc = {zero, zero, zero, zero};
         if (ip < P) {
-          gamma = bmul(ci, binv(B[ip]));
-          gamma = {-gamma.a, -gamma.b, -gamma.c, -gamma.d};
-        }
-        Blk nb = B[i];
-        Blk t1 = bmul(alpha, C[im]);
-        nb = {nb.a + t1.a, nb.b + t1.b, nb.c + t1.c, nb.d + t1.d};
-        double2 nd = D[i];
-        double2 v1 = bvec(alpha, D[im]);
-        nd.x += v1.x;
-        nd.y += v1.y;
-        Blk na = bmul(alpha, A[im]);
-        Blk nc = {0, 0, 0, 0};
-        if (ip < P) {
-          Blk t2 = bmul(gamma, A[ip]);
-          nb = {nb.a + t2.a, nb.b + t2.b, nb.c + t2.c, nb.d + t2.d};
-          double2 v2 = bvec(gamma, D[ip]);
-          nd.x += v2.x;
-          nd.y += v2.y;
+          const Blk gamma = bneg(bmul(C[i], binv(B[ip])));
+          nb = badd(nb, bmul(gamma, A[ip]));
+          nd = vadd(nd, bvec(gamma, D[ip]));
           nc = bmul(gamma, C[ip]);
         }
         B[i] = nb;
@@ -231,17 +237,9 @@ __global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_a
     for (int s = P / 2; s >= 1; s /= 2) {
       for (int t = threadIdx.x; t < P / (2 * s); t += blockDim.x) {
         const int i = 2 * s * t + s - 1;
-        double2 rhs = D[i];
-        if (i - s >= 0) {
-          double2 v = bvec(A[i], D[i - s]);
-          rhs.x -= v.x;
-          rhs.y -= v.y;
-        }
-        if (i + s < P) {
-          double2 v = bvec(C[i], D[i + s]);
-          rhs.x -= v.x;
-          rhs.y -= v.y;
-        }
+        Vec2 rhs = D[i];
+        if (i - s >= 0) rhs = vsub(rhs, bvec(A[i], D[i - s]));
+        if (i + s < P) rhs = vsub(rhs, bvec(C[i], D[i + s]));
         D[i] = bvec(binv(B[i]), rhs);
       }
       __syncthreads();
@@ -255,13 +253,13 @@ __global__ void __launch_bounds__(256) als_kernel(const double* __restrict__ y_a
     // same z, so the remaining iterations are skipped
     int changed = 0;
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      const double nw = (y[j] > z[j]) ? p : 1.0 - p;
-      changed |= nw != w[j];
+      const df nw = dgt(y[j], z[j]) ? wp : wq;
+      changed |= (nw.h != w[j].h) || (nw.l != w[j].l);
       w[j] = nw;
     }
     if (!__syncthreads_or(changed)) break;
   }
-  for (int j = threadIdx.x; j < m; j += blockDim.x) z_all[(int64_t)row * m + j] = z[j];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) z_all[(int64_t)row * m + j] = dw::to_double(z[j]);
 }
 
 // -------------------------------------------------------------- ridge ---
@@ -539,7 +537,7 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
     FKK_COUNT_LAUNCH(); small_gemm_kernel<<<dim3(nq_max, 4), 256, k * sizeof(double), st>>>(x_rows, hb, k, m, phph, nq_dev);
     int P = 1;
     while (P < (m + 1) / 2) P *= 2;
-    size_t als_smem = (size_t)P * (3 * sizeof(Blk) + sizeof(double2)) + (size_t)6 * P * sizeof(double);
+    size_t als_smem = (size_t)P * (3 * sizeof(Blk) + sizeof(Vec2)) + (size_t)6 * P * sizeof(df);
     FKK_CUDA(ctx, cudaFuncSetAttribute(als_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)als_smem));
     FKK_COUNT_LAUNCH(); als_kernel<<<nq_max, 256, als_smem, st>>>(phph, m, P, bp.als_lambda, bp.als_p, bp.als_iters, perr, nq_dev);
     const size_t rsm = (size_t)(k * k + k * nq_max + k) * sizeof(dw::df);
