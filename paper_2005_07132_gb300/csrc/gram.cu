@@ -8,15 +8,15 @@
 // sum of products of rounding residuals, 2^-16 below the other terms and of
 // either sign; on the diagonal it would be a positive bias of ~2^-18 sum d^2,
 // so the diagonal is taken instead from the exact sum_n d_j^2 of the
-// transform (fp32 within a 64-row tile, fp64 across tiles).  On the test
+// transform (fp32 within a 64-row tile, double-word across tiles).  On the test
 // cubes this leaves the spectral-norm error of G where four products put it
 // (1e-7 of ||G||).  The rectangular A^T Q of the randomised SVD keeps all
 // four products.  Output tiles are
 // 128 (rows i) x 256 (columns j) covering the upper triangle (i-block 128*ib
 // < 256*(jb+1)); the contraction over spectra is split into `splits`
 // contiguous ranges, one CTA per (tile, split), and the fp32 partial tiles
-// are summed in fp64 in a fixed order by the assemble kernel, which also
-// adds the shift terms and the f(w) scaling.
+// are summed in a fixed order, in double-word arithmetic, by the assemble
+// kernel, which also adds the shift terms and the f(w) scaling.
 //
 // CTA = 4 warps.  Warp 0 lane 0 issues TMA loads of 64-spectrum K-blocks
 // (A: 128 channels, B: 256 channels, hi and lo) into a 2-stage ring; warp 1
