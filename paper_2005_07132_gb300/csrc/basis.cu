@@ -62,31 +62,46 @@ __global__ void gather_rows_kernel(const float* __restrict__ p, int k, const int
 // ------------------------------------------------------------- Hilbert ---
 // One block per row: edge-replicated centred padding to L, FFT, -i sgn(m),
 // inverse FFT, crop.  rows_dev (optional) bounds the live rows.
-__global__ void hilbert_rows_f64_kernel(const double* __restrict__ x, int m, int L, double* __restrict__ h,
-                                        const int* __restrict__ rows_dev) {
-  extern __shared__ double2 zsm[];
+// e^{-2 pi i t / L} for t < L as double-word pairs (fp64 sincospi, split).
+__global__ void twiddle_dz_kernel(dz* __restrict__ tw, int L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  double s, c;
+  sincospi(-2.0 * (double)t / (double)L, &s, &c);
+  const df cd = dw::from_double(c), sd = dw::from_double(s);
+  tw[t] = {make_float2(cd.h, sd.h), make_float2(cd.l, sd.l)};
+}
+
+// H{x} of each row (the padded discrete Hilbert transform of Eq. KCARS) in
+// double-word complex arithmetic: edge-replicated to L, forward FFT,
+// multiplier -i sgn, inverse FFT, cropped and scaled by 1/L.
+__global__ void hilbert_rows_kernel(const double* __restrict__ x, int m, int L, const dz* __restrict__ twg,
+                                    double* __restrict__ h, const int* __restrict__ rows_dev) {
+  extern __shared__ dz zsm[];
   const int row = blockIdx.x;
   if (rows_dev && row >= *rows_dev) return;
-  double2* tw = zsm;
-  double2* b0 = zsm + L;
-  double2* b1 = b0 + L;
-  fill_twiddles_f64(tw, L);
+  dz* tw = zsm;
+  dz* b0 = zsm + L;
+  dz* b1 = b0 + L;
   const int left = (L - m) / 2;
   const double* xr = x + (int64_t)row * m;
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    int s = min(max(t - left, 0), m - 1);
-    b0[t] = make_double2(xr[s], 0.0);
+    tw[t] = twg[t];
+    const int s = min(max(t - left, 0), m - 1);
+    const df v = dw::from_double(xr[s]);
+    b0[t] = {make_float2(v.h, 0.f), make_float2(v.l, 0.f)};
   }
   __syncthreads();
-  int cur = fft_block_f64<-1>(b0, b1, L, tw, threadIdx.x, blockDim.x);
-  double2* X = cur ? b1 : b0;
-  double2* Y = cur ? b0 : b1;
-  for (int t = threadIdx.x; t < L; t += blockDim.x) X[t] = hilbert_mult_f64(X[t], t, L);
+  int cur = fft_block_dz<-1>(b0, b1, L, tw, threadIdx.x, blockDim.x);
+  dz* X = cur ? b1 : b0;
+  dz* Y = cur ? b0 : b1;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) X[t] = hilbert_mult_dz(X[t], t, L);
   __syncthreads();
-  int cur2 = fft_block_f64<+1>(X, Y, L, tw, threadIdx.x, blockDim.x);
-  double2* H = cur2 ? Y : X;
+  int cur2 = fft_block_dz<+1>(X, Y, L, tw, threadIdx.x, blockDim.x);
+  dz* H = cur2 ? Y : X;
   const double invL = 1.0 / (double)L;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) h[(int64_t)row * m + j] = H[left + j].x * invL;
+  for (int j = threadIdx.x; j < m; j += blockDim.x)
+    h[(int64_t)row * m + j] = dw::to_double(dw::make(H[left + j].h.x, H[left + j].l.x)) * invL;
 }
 
 // ---------------------------------------------------------- small ops ---
@@ -498,9 +513,13 @@ fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmi
 
 static fkk_status hilbert_rows(fkk_ctx* ctx, const double* x, int rows, int m, int L, double* h, const int* rows_dev,
                                cudaStream_t st) {
-  size_t smem = (size_t)3 * L * sizeof(double2);
-  FKK_CUDA(ctx, cudaFuncSetAttribute(hilbert_rows_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FKK_COUNT_LAUNCH(); hilbert_rows_f64_kernel<<<rows, 256, smem, st>>>(x, m, L, h, rows_dev);
+  fkk_status s;
+  dz* tw = (dz*)workspace(ctx, "hilb_tw", (size_t)L * sizeof(dz), &s);
+  if (!tw) return s;
+  FKK_COUNT_LAUNCH(); twiddle_dz_kernel<<<(L + 255) / 256, 256, 0, st>>>(tw, L);
+  size_t smem = (size_t)3 * L * sizeof(dz);
+  FKK_CUDA(ctx, cudaFuncSetAttribute(hilbert_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FKK_COUNT_LAUNCH(); hilbert_rows_kernel<<<rows, 256, smem, st>>>(x, m, L, tw, h, rows_dev);
   return cuda_check(ctx, cudaGetLastError(), "hilbert_rows launch");
 }
 

@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+
 namespace fkk {
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -143,58 +145,62 @@ __device__ __forceinline__ float2 hilbert_mult(float2 z, int m, int L) {
   return (2 * m < L) ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
 }
 
-// ---------------------------------------------------------------- fp64 ---
-// Double-precision variants for the k basis vectors (a few rows of length L).
-__device__ __forceinline__ double2 z_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 z_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+// ------------------------------------------------------- double-word ---
+// Double-word complex variants for the k basis vectors (a few rows of length
+// L): a complex number is a dw2 pair, lane x the real part and lane y the
+// imaginary part (about 48 bits each), on the fp32 pipe -- this part's fp64
+// rate would make an fp64 transform of the rows several times slower.
+using dz = dw2::df2;
+
+__device__ __forceinline__ dz dz_mul(dz a, dz b) {
+  // (re a re b - im a im b, re a im b + im a re b)
+  const dz ar = {make_float2(a.h.x, a.h.x), make_float2(a.l.x, a.l.x)};
+  const dz ai = {make_float2(a.h.y, a.h.y), make_float2(a.l.y, a.l.y)};
+  const dz bs = {make_float2(-b.h.y, b.h.x), make_float2(-b.l.y, b.l.x)};
+  return dw2::add(dw2::mul(ar, b), dw2::mul(ai, bs));
 }
 
-// One radix-2 Stockham pass in double precision (same indexing as above).
+// One radix-2 Stockham pass (same indexing as above).
 template <int SIGN>
-__device__ __forceinline__ void stockham_pass2_f64(const double2* __restrict__ x, double2* __restrict__ y, int L,
-                                                   int Ns, const double2* __restrict__ tw, int t0, int nt) {
+__device__ __forceinline__ void stockham_pass2_dz(const dz* __restrict__ x, dz* __restrict__ y, int L, int Ns,
+                                                  const dz* __restrict__ tw, int t0, int nt) {
   const int LR = L / 2;
   const int tws = L / (Ns * 2);
   for (int j = t0; j < LR; j += nt) {
     const int k = j & (Ns - 1);
-    double2 a = x[j], b = x[j + LR];
+    const dz a = x[j];
+    dz b = x[j + LR];
     if (Ns > 1) {
-      double2 w = tw[k * tws];
-      if (SIGN > 0) w.y = -w.y;
-      b = z_mul(b, w);
+      dz w = tw[k * tws];
+      if (SIGN > 0) {
+        w.h.y = -w.h.y;
+        w.l.y = -w.l.y;
+      }
+      b = dz_mul(b, w);
     }
     const int base = (j - k) * 2 + k;
-    y[base] = z_add(a, b);
-    y[base + Ns] = z_sub(a, b);
+    y[base] = dw2::add(a, b);
+    y[base + Ns] = dw2::sub(a, b);
   }
 }
 
 template <int SIGN>
-__device__ __forceinline__ int fft_block_f64(double2* buf0, double2* buf1, int L, const double2* tw, int t0,
-                                             int nt) {
-  double2* bufs[2] = {buf0, buf1};
+__device__ __forceinline__ int fft_block_dz(dz* buf0, dz* buf1, int L, const dz* tw, int t0, int nt) {
+  dz* bufs[2] = {buf0, buf1};
   int cur = 0;
   for (int Ns = 1; Ns < L; Ns *= 2) {
-    stockham_pass2_f64<SIGN>(bufs[cur], bufs[cur ^ 1], L, Ns, tw, t0, nt);
+    stockham_pass2_dz<SIGN>(bufs[cur], bufs[cur ^ 1], L, Ns, tw, t0, nt);
     cur ^= 1;
     __syncthreads();
   }
   return cur;
 }
 
-__device__ __forceinline__ void fill_twiddles_f64(double2* tw, int L) {
-  for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)t / (double)L, &s, &c);
-    tw[t] = make_double2(c, s);
-  }
-}
-
-__device__ __forceinline__ double2 hilbert_mult_f64(double2 z, int m, int L) {
-  if (m == 0 || 2 * m == L) return make_double2(0.0, 0.0);
-  return (2 * m < L) ? make_double2(z.y, -z.x) : make_double2(-z.y, z.x);
+// Multiply by -i*sgn(m) (0 at DC and Nyquist), exactly.
+__device__ __forceinline__ dz hilbert_mult_dz(dz z, int m, int L) {
+  if (m == 0 || 2 * m == L) return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  if (2 * m < L) return {make_float2(z.h.y, -z.h.x), make_float2(z.l.y, -z.l.x)};
+  return {make_float2(-z.h.y, z.h.x), make_float2(-z.l.y, z.l.x)};
 }
 
 }  // namespace fkk
