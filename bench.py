@@ -11,10 +11,15 @@ on the basis, reconstruction.
 
 Printed (one JSON line, rank 0): value = fKK-EC spectra/s of the whole job,
 the per-stage breakdown, the roofline of the dominant stage, the same metric
-end to end through pinned host buffers (e2e), the FP64 CPU oracle on a
-bounded sample of the same cube (cpu_baseline), the per-spectrum KK and the
-ML apply throughput on the same cube, clocks sampled during the timed
-region, and the number of library kernels launched in it.
+end to end through pinned host buffers (e2e: pipelined as a stream of cubes
+runs, with the in-order figure beside it), the FP64 CPU oracle on a bounded
+sample of the same cube (cpu_baseline), the per-spectrum KK and the ML apply
+throughput on the same cube, the fit with the randomised SVD, the
+conventional workflow (with and without the SVD denoising of the raw
+spectra), serving latency and throughput, the speed-enhancement curve on the
+simulation-shaped workload, clocks sampled during the timed region, and the
+number of library kernels launched in it.  --svd randomized makes the
+randomised SVD the timed fit.
 
 --impl reference times the oracle itself (plain FP64 numpy) as the reference
 arm: each step is an oracle fit of a bounded sample of the same workload.
