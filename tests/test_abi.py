@@ -50,3 +50,38 @@ def test_create_rejects_bad_arguments():
     assert L.fkk_create(C.byref(h), -1, 0) == -1
     assert L.fkk_destroy(None) == 0
     assert L.kk_per_spectrum(None, None, 1, 1, 1, None, 0, 1e-6, None, None, 1, None) == -1
+
+
+def _header_struct_fields(name):
+    """Field names of a typedef'd struct in include/fkk.h, in order."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fkk.h")).read()
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*" + name + ";", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            fields.append(decl.split()[-1])
+    return fields
+
+
+def test_fit_params_layout_matches_the_library():
+    """The ctypes mirror of fkk_fit_params has the compiled struct's size and
+    the header's fields in the header's order."""
+    from paper_2005_07132_gb300 import _lib
+    L = _lib.lib()
+    assert C.sizeof(_lib.FitParams) == L.fkk_fit_params_size()
+    assert [f[0] for f in _lib.FitParams._fields_] == _header_struct_fields("fkk_fit_params")
+
+
+def test_fit_params_defaults():
+    """fkk_fit_params_default gives the defaults the header documents."""
+    from paper_2005_07132_gb300 import _lib
+    p = _lib.fit_params()
+    assert (p.k, p.pad_len, p.pec, p.sec, p.als_iters, p.sg_order) == (20, 0, 1, 1, 20, 2)
+    assert abs(p.als_p - 0.01) < 1e-15 and abs(p.ridge_rel - 1e-3) < 1e-15 and p.ml_lambda == 0.0
+    assert abs(p.ratio_floor - 1e-6) < 1e-12
+    assert (p.k_max, p.rank_eps, p.svd, p.rsvd_oversample, p.rsvd_power_iters, p.rsvd_seed) == (80, 0.0, 0, 10, 2, 0)
+    assert p.denoise_k == 0
