@@ -34,6 +34,15 @@ fkk_status side_stream(fkk_ctx* ctx, cudaStream_t* out) {
   *out = ctx->aux;
   return FKK_OK;
 }
+bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of a pointer the runtime does not know
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
 fkk_status bind(fkk_ctx* ctx) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   return cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");

@@ -282,6 +282,51 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   FKK_TRY(check_params(ctx, *params, m, n));
   FKK_TRY(bind(ctx));
   cudaStream_t st = as_stream(stream);
+  // Host buffers (pinned or pageable) are staged through the context's
+  // workspace on `stream`: inputs copied in before the transform, outputs
+  // copied back after the reconstruction.  Device pointers are used in place.
+  const bool im_on_host = im_out && is_host_ptr(im_out), re_on_host = re_out && is_host_ptr(re_out);
+  if ((im_out && re_out) && im_on_host != re_on_host)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_fit_basis: im_out and re_out must both be host or both device memory");
+  float* im_host = nullptr;
+  float* re_host = nullptr;
+  const int64_t ld_host = ld_out;
+  {
+    fkk_status sh;
+    if (is_host_ptr(i_cars)) {
+      float* d = (float*)workspace(ctx, "fit_host_x", (size_t)n * m * 4, &sh);
+      if (!d) return sh;
+      FKK_CUDA(ctx, cudaMemcpy2DAsync(d, (size_t)m * 4, i_cars, (size_t)ld * 4, (size_t)m * 4, (size_t)n,
+                                      cudaMemcpyHostToDevice, st));
+      i_cars = d;
+      ld = m;
+    }
+    if (is_host_ptr(i_ref)) {
+      float* d = (float*)workspace(ctx, "fit_host_ref", (size_t)m * 4, &sh);
+      if (!d) return sh;
+      FKK_CUDA(ctx, cudaMemcpyAsync(d, i_ref, (size_t)m * 4, cudaMemcpyHostToDevice, st));
+      i_ref = d;
+    }
+    if (f_or_null && is_host_ptr(f_or_null)) {
+      float* d = (float*)workspace(ctx, "fit_host_f", (size_t)m * 4, &sh);
+      if (!d) return sh;
+      FKK_CUDA(ctx, cudaMemcpyAsync(d, f_or_null, (size_t)m * 4, cudaMemcpyHostToDevice, st));
+      f_or_null = d;
+    }
+    if (im_on_host || re_on_host) {
+      if (im_out) {
+        im_host = im_out;
+        im_out = (float*)workspace(ctx, "fit_host_im", (size_t)n * m * 4, &sh);
+        if (!im_out) return sh;
+      }
+      if (re_out) {
+        re_host = re_out;
+        re_out = (float*)workspace(ctx, "fit_host_re", (size_t)n * m * 4, &sh);
+        if (!re_out) return sh;
+      }
+      ld_out = m;
+    }
+  }
   fkk_fit_params p = *params;  // k is filled in below when chosen by the rank rule
   const bool autok = p.k == 0;
   int k = p.k;
@@ -385,6 +430,14 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   stage_mark(ctx, 5, st);
   if (im_out) {
     if ((s = launch_reconstruct(ctx, P, n, k, m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st))) return bail(s);
+    if (im_host &&
+        (s = cuda_check(ctx, cudaMemcpy2DAsync(im_host, (size_t)ld_host * 4, im_out, (size_t)m * 4, (size_t)m * 4,
+                                               (size_t)n, cudaMemcpyDeviceToHost, st), "copy Im to host")))
+      return bail(s);
+    if (re_host &&
+        (s = cuda_check(ctx, cudaMemcpy2DAsync(re_host, (size_t)ld_host * 4, re_out, (size_t)m * 4, (size_t)m * 4,
+                                               (size_t)n, cudaMemcpyDeviceToHost, st), "copy Re to host")))
+      return bail(s);
   }
   stage_mark(ctx, 6, st);
   if ((s = cuda_check(ctx, cudaGetLastError(), "fkk_fit_basis"))) return bail(s);

@@ -67,6 +67,10 @@ fkk_status bind(fkk_ctx* ctx);
 // The context's side stream (created on first use, with its fork / join events).
 fkk_status side_stream(fkk_ctx* ctx, cudaStream_t* out);
 
+// Whether p points to host memory (pinned or pageable) rather than device or
+// managed memory.
+bool is_host_ptr(const void* p);
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Record the boundary event `i` of the fit's stages when timing is on.

@@ -318,3 +318,31 @@ def test_fit_full_size_703026x1000_sampled(fk, ctx):
     got = im[torch.from_numpy(rows).cuda()].cpu().numpy()
     assert rel_l2(got, res["im"]) <= 1e-4
     np.testing.assert_array_equal(basis.get("q").astype(np.int64), res["q"])
+
+
+def test_fit_with_host_buffers(fk, ctx, cube1):
+    """Host inputs and outputs (pinned and pageable, a strided cube) go
+    through the same kernels: the output equals the device-buffer fit's bit
+    for bit."""
+    x = torch.from_numpy(np.ascontiguousarray(cube1.i_cars))
+    r = torch.from_numpy(np.ascontiguousarray(cube1.i_ref))
+    prm = fk.fit_params(k=20)
+    b0, im0, _ = fk.fkk_fit_basis(ctx, x.cuda(), r.cuda(), prm)
+    torch.cuda.synchronize()
+    ref = im0.cpu()
+    n, m = x.shape
+    padded = torch.zeros((n, m + 3), dtype=torch.float32)
+    padded[:, :m] = x
+    for xh, rh, pin in ((x.pin_memory(), r.pin_memory(), True), (x.clone(), r.clone(), False),
+                        (padded[:, :m], r.clone(), False)):
+        oh = torch.full((n, m), float("nan"))
+        if pin:
+            oh = oh.pin_memory()
+        b1, im1, _ = fk.fkk_fit_basis(ctx, xh, rh, prm, im_out=oh)
+        torch.cuda.synchronize()
+        assert torch.equal(im1, ref)
+        b1.close()
+    with pytest.raises(fk.FkkError):
+        fk.fkk_fit_basis(ctx, x.cuda(), r.cuda(), prm, im_out=torch.empty((n, m)),
+                         re_out=torch.empty((n, m), device="cuda"))
+    b0.close()
