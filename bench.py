@@ -483,6 +483,30 @@ def run_ours(args, rank, world, local):
                        "mode": "pipelined: upload of step i and download of step i-1 beside the fit (3 streams)",
                        "serial": {"value": world * n / (serial_ms / 1e3), "ms_per_step": serial_ms,
                                   "mode": "upload, fit, download in order on one stream"}}
+        # the C ABI called with the pinned host buffers themselves (the library
+        # copies them in and the output back on the fit's stream)
+        try:
+            def host_step():
+                b, _, _ = fk.fkk_fit_basis(ctx, xh, refh, prm, im_out=oh, stream=st)
+                return b
+
+            for _ in range(2):
+                bases.append(host_step())
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(args.steps):
+                bases.append(host_step())
+            e1.record(st)
+            torch.cuda.synchronize()
+            host_ms = e0.elapsed_time(e1) / args.steps
+            line["e2e"]["c_abi_host_buffers"] = {
+                "value": world * n / (host_ms / 1e3), "ms_per_step": host_ms,
+                "mode": "fkk_fit_basis on the pinned host cube and output, in order on one stream"}
+        except Exception as exc:  # reported, not fatal: the other figures stand
+            line["e2e"]["c_abi_host_buffers"] = {"error": str(exc)[:200]}
+        for b in bases:
+            b.close()
+        bases.clear()
 
         # ---- per-spectrum KK and ML apply on the same cube ----
         def timed(fn, reps=5):
