@@ -265,24 +265,24 @@ __global__ void __launch_bounds__(kFinThreads) conv_finish_kernel(FinArgs p, int
     }
     // K_pec of both spectra
     for (int j = t0; j < M; j += tpf) {
-      const float r = p.i_ref[j];
+      const float r = 1.0f / p.i_ref[j];
       for (int q = 0; q < 2; ++q) {
         const bool ok = q == 0 ? live : has1;
         float re = 0.f, im = 0.f;
         if (ok) {
           const int64_t nq = q == 0 ? n0 : n1;
-          float x = p.i_cars[nq * p.ld + j] / r;
+          float x = p.i_cars[nq * p.ld + j] * r;
           if (!(x >= p.floor_)) x = p.floor_;
-          const float av = 0.5f * logf(x);
+          const float av = 0.34657359027997264f * __log2f(x);  // as kk_per_spectrum
           float hv = 0.f, pe = 0.f;
           if (p.perr) {
             const float2 hh = hb[left + j];
             hv = (q == 0 ? hh.x : hh.y) * invL;
             pe = p.perr[nq * M + j];
           }
-          const float amp = expf(av + hv);
-          float sn, cs;
-          sincosf(p.phi[nq * M + j] - pe, &sn, &cs);
+          const float amp = exp2f(1.4426950408889634f * (av + hv));
+          const float ph = p.phi[nq * M + j] - pe;
+          const float sn = __sinf(ph), cs = __cosf(ph);
           re = amp * cs;
           im = amp * sn;
         }

@@ -128,6 +128,12 @@ fkk_status launch_reconstruct_tc_scratch(fkk_ctx* ctx, const float* p, int64_t n
 
 // The per-spectrum KK kernel in its phase mode: phi = H{1/2 ln max(I/I_ref,
 // floor)} for n spectra, written with row stride ld_phi.
+// Register-FFT per-spectrum KK for pad lengths 1024 and 2048 (one warp per
+// pair of spectra); *handled is false (and nothing is launched) otherwise.
+fkk_status launch_kk_warp(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld, const float* i_ref,
+                          int L, float floor_, float* im, float* re, int64_t ld_out, bool phase, cudaStream_t st,
+                          bool* handled);
+
 fkk_status launch_kk_phase(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
                            const float* i_ref, int L, float floor_, float* phi, int64_t ld_phi,
                            cudaStream_t st);

@@ -10,7 +10,7 @@
 // spectrum pairs in a grid-stride loop.  The same kernel, in its phase mode,
 // writes phi = H{a} itself for the conventional workflow's PEC.
 #include "fft.cuh"
-#include "fkk_internal.h"
+#include "fit.h"
 
 namespace fkk {
 namespace {
@@ -60,17 +60,17 @@ __global__ void __launch_bounds__(kThreads) kk_pairs_kernel(KKArgs p, int tpf) {
     const bool has1 = live && n1 < p.n;
     // log ratio of both spectra
     for (int j = t0; j < M; j += tpf) {
-      float r = p.i_ref[j];
+      const float r = 1.0f / p.i_ref[j];
       float v0 = 0.f, v1 = 0.f;
       if (live) {
-        float x = p.i_cars[n0 * p.ld + j] / r;
+        float x = p.i_cars[n0 * p.ld + j] * r;
         if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
-        v0 = 0.5f * logf(x);
+        v0 = 0.34657359027997264f * __log2f(x);  // (ln 2 / 2) log2
       }
       if (has1) {
-        float x = p.i_cars[n1 * p.ld + j] / r;
+        float x = p.i_cars[n1 * p.ld + j] * r;
         if (!(x >= p.floor_)) { x = p.floor_; ++clamped; }
-        v1 = 0.5f * logf(x);
+        v1 = 0.34657359027997264f * __log2f(x);
       }
       a0[j] = v0;
       a1[j] = v1;
@@ -97,18 +97,16 @@ __global__ void __launch_bounds__(kThreads) kk_pairs_kernel(KKArgs p, int tpf) {
       }
     } else if (live) {
       for (int j = t0; j < M; j += tpf) {
-        float2 h = H[left + j];
-        float s0, c0;
-        sincosf(h.x * invL, &s0, &c0);
-        float e0 = expf(a0[j]);
-        p.im[n0 * p.ld_out + j] = e0 * s0;
-        if (p.re) p.re[n0 * p.ld_out + j] = e0 * c0;
+        // the same operations as the register-FFT kernel (bit-identical outputs)
+        const float2 h = H[left + j];
+        const float ph0 = h.x * invL, ph1 = h.y * invL;
+        const float e0 = exp2f(1.4426950408889634f * a0[j]);
+        p.im[n0 * p.ld_out + j] = e0 * __sinf(ph0);
+        if (p.re) p.re[n0 * p.ld_out + j] = e0 * __cosf(ph0);
         if (has1) {
-          float s1, c1;
-          sincosf(h.y * invL, &s1, &c1);
-          float e1 = expf(a1[j]);
-          p.im[n1 * p.ld_out + j] = e1 * s1;
-          if (p.re) p.re[n1 * p.ld_out + j] = e1 * c1;
+          const float e1 = exp2f(1.4426950408889634f * a1[j]);
+          p.im[n1 * p.ld_out + j] = e1 * __sinf(ph1);
+          if (p.re) p.re[n1 * p.ld_out + j] = e1 * __cosf(ph1);
         }
       }
     }
@@ -130,6 +128,9 @@ template <bool kPhase>
 static fkk_status launch_kk_impl(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, int64_t ld,
                                  const float* i_ref, int L, float floor_, float* im, float* re,
                                  int64_t ld_out, cudaStream_t st) {
+  bool handled = false;
+  fkk_status ws = launch_kk_warp(ctx, i_cars, n, m, ld, i_ref, L, floor_, im, re, ld_out, kPhase, st, &handled);
+  if (handled) return ws;
   int tpf = L / 8;
   if (tpf > kThreads) tpf = kThreads;
   if (tpf < 32) tpf = 32;
