@@ -137,7 +137,21 @@ fkk_status kk_per_spectrum(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra,
 /* ------------------------------------------------------------------ */
 
 enum { FKK_SEC_SAVGOL = 0, FKK_SEC_MEAN = 1 };
-enum { FKK_PREC_BF16X3 = 0 /* fp32-accurate: 3 bf16 products per term */ };
+/* Arithmetic of ML:fKK-EC apply (fkk_apply and the serving loop; Sec. 2.6),
+ * whose two GEMMs -- the projection of the raw spectra and the
+ * reconstruction -- run on the tensor cores with fp32 accumulation and an
+ * fp32 exp / sin epilogue, on log ratios shifted by the basis' offset
+ * (fkk_basis_set_offset):
+ *   FKK_PREC_BF16X3  operands split into bf16 hi + lo, three products per
+ *                    GEMM (hi.hi + hi.lo + lo.hi): fp32-accurate;
+ *   FKK_PREC_BF16    the reduced-precision served form: projection with one
+ *                    bf16 product, reconstruction with two (P hi + lo times
+ *                    bf16 coefficients) -- half the tensor work; relative L2
+ *                    error of Im about 1e-3 or below.
+ * The fit (Gram, eigensolve, the fit's projection and reconstruction) is
+ * fp32-accurate in both.  Where the fused apply kernel cannot run (see
+ * fkk_apply) the apply is fp32-accurate in both. */
+enum { FKK_PREC_BF16X3 = 0, FKK_PREC_BF16 = 1 };
 
 typedef struct {
   int32_t k;            /* kept basis vectors, 1..80; 0 = chosen by the rank rule (k_max, rank_eps) */
@@ -152,7 +166,7 @@ typedef struct {
   int32_t sg_window;    /* odd Savitzky-Golay window <= M; 0 = largest odd <= M/2 */
   int32_t sg_order;     /* Savitzky-Golay polynomial order, < window, <= 7 */
   double ml_lambda;     /* ridge lambda of Eq. ML_Unew used by fkk_apply (>= 0) */
-  int32_t precision;    /* FKK_PREC_BF16X3 */
+  int32_t precision;    /* FKK_PREC_BF16X3 or FKK_PREC_BF16: arithmetic of fkk_apply with the basis */
   float ratio_floor;    /* I/I_ref is clamped to >= ratio_floor before the log (> 0) */
   double noise_alpha;   /* Poisson multiplier alpha of f(w) (Sec. 2.2); used when f is NULL */
   double noise_sigma_g; /* Gaussian sigma_g of f(w); alpha = sigma_g = 0 means f = 1 */
@@ -229,7 +243,12 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, i
 /* ML:fKK-EC (Sec. 2.6): U_new S = A_new V diag(s^2/(s^2+ml_lambda)) with the
  * basis's f, I_ref and ratio floor (Eq. ML_Unew), then Eq. fKKEC with the
  * trained C_amp, C_ph.  i_cars has basis n_channels columns.  re_out may be
- * NULL.  Errors: FKK_ERR_INVALID_ARG, FKK_ERR_BUDGET, FKK_ERR_CUDA. */
+ * NULL.  With row strides that are multiples of 4 floats, 16-byte aligned
+ * device arrays and k <= 62 this is one launch that reads I once and writes
+ * Im (and Re) once, in the basis' precision; otherwise a projection kernel
+ * and the reconstruction (fp32-accurate).  The first call packs the basis'
+ * operands on the device (a synchronisation of `stream`).  Errors:
+ * FKK_ERR_INVALID_ARG, FKK_ERR_BUDGET, FKK_ERR_CUDA. */
 fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* basis, const float* i_cars, int64_t n_spectra, int64_t ld,
                      float* im_out, float* re_out, int64_t ld_out, void* stream);
 
@@ -254,6 +273,23 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t n_channels, const fkk_fit
 
 /* sizeof(fkk_fit_params) as compiled into the library (ABI check). */
 size_t fkk_fit_params_size(void);
+
+/* Set the per-channel offset (n_channels doubles, HOST memory) that
+ * fkk_apply subtracts from the log ratios before rounding them to bf16 and
+ * adds back exactly through the reconstruction (the results are the same
+ * up to rounding for any offset; the closer it is to typical spectra, the
+ * smaller the rounding error of the reduced-precision form).  fkk_fit_basis
+ * stores the training mean of 1/2 ln max(I/I_ref, floor); a basis built by
+ * fkk_basis_from_arrays starts with 0.  Synchronises the basis' device.
+ * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_CUDA. */
+fkk_status fkk_basis_set_offset(fkk_basis* basis, const double* offset, int32_t n_channels);
+
+/* Set the precision (FKK_PREC_BF16X3 or FKK_PREC_BF16) that fkk_apply and
+ * the serving loop use with this basis; the trained arrays are unchanged,
+ * so one basis can be served in either form (Sec. 2.6 reuses it as is).
+ * Not to be called while work on the basis is queued.  Errors:
+ * FKK_ERR_INVALID_ARG. */
+fkk_status fkk_basis_set_precision(fkk_basis* basis, int32_t precision);
 
 /* Release a basis (NULL is ok).  Synchronises the basis's device. */
 void fkk_basis_free(fkk_basis* basis);

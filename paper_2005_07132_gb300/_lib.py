@@ -60,6 +60,8 @@ SIGNATURES = {
     "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
     "fkk_apply": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64, _P]),
     "fkk_basis_free": (None, [_P]),
+    "fkk_basis_set_precision": (_I32, [_P, _I32]),
+    "fkk_basis_set_offset": (_I32, [_P, _P, _I32]),
     "fkk_basis_info": (_I32, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     "fkk_basis_get": (_I32, [_P, _I32, _P, _SZ]),
     "fkk_basis_from_arrays": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, C.POINTER(_P)]),
@@ -97,6 +99,7 @@ class FitParams(C.Structure):
 
 
 SEC_SAVGOL, SEC_MEAN = 0, 1
+PREC_BF16X3, PREC_BF16 = 0, 1
 SVD_EXACT, SVD_RANDOMIZED = 0, 1
 ART = {name: i for i, name in enumerate(
     ["s", "lambda", "v", "f", "b", "h_b", "phi_pec", "h_phi", "v_sec", "c_amp", "c_ph", "q", "energy"])}
@@ -305,6 +308,22 @@ class Basis:
         if st != FKK_OK:
             raise FkkError(st, "fkk_basis_info")
         return {"n_channels": m.value, "k": k.value, "pad_len": L.value, "nq": nq.value}
+
+    def set_precision(self, precision: int):
+        """Arithmetic of fkk_apply with this basis (fkk_basis_set_precision)."""
+        st = lib().fkk_basis_set_precision(self._h, int(precision))
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_basis_set_precision")
+
+    def set_offset(self, offset):
+        """Per-channel offset of the log ratios used by fkk_apply
+        (fkk_basis_set_offset; host float64, n_channels values)."""
+        import numpy as np
+
+        o = np.ascontiguousarray(offset, np.float64)
+        st = lib().fkk_basis_set_offset(self._h, o.ctypes.data_as(C.c_void_p), o.size)
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_basis_set_offset")
 
     def training_residual(self) -> float:
         """1 - sum(lambda_1..k) / ||A||_F^2 of the training cube: the residual

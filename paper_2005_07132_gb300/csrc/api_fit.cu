@@ -11,28 +11,7 @@
 #include "common.cuh"
 #include "fit.h"
 
-struct fkk_basis {
-  int device = 0;
-  int m = 0, k = 0, L = 0;
-  fkk_fit_params params{};
-  double* f = nullptr;      // m (always materialised, 1 when f = 1)
-  double* lam = nullptr;    // k
-  double* s = nullptr;      // k
-  double* v = nullptr;      // m x k
-  double* w = nullptr;      // m x k: V diag(s^2/(s^2+ml_lambda))
-  double* b = nullptr;      // k x m each below
-  double* h_b = nullptr;
-  double* phi_pec_t = nullptr;
-  double* h_phi = nullptr;
-  double* v_sec_t = nullptr;
-  double* c_amp = nullptr;
-  double* c_ph = nullptr;
-  int64_t* q = nullptr;     // up to 2k
-  int* nq = nullptr;        // device count
-  double* energy = nullptr; // trace(A^T A) of the training cube (in the pad after nq)
-  float* i_ref = nullptr;   // m
-  void* block = nullptr;    // single allocation backing all of the above
-};
+#include "basis_internal.h"
 
 namespace fkk {
 namespace {
@@ -49,6 +28,14 @@ __global__ void s_and_w_kernel(const double* __restrict__ lam, const double* __r
   const double shrink = (l + ml_lambda) > 0.0 ? l / (l + ml_lambda) : 0.0;
   if (threadIdx.x == 0) s[i] = sqrt(l);
   for (int j = threadIdx.x; j < m; j += blockDim.x) w[(int64_t)j * k + i] = v[(int64_t)j * k + i] * shrink;
+}
+
+// Training mean of the log ratios per channel, 1/2 ln max(I/I_ref, floor):
+// the transform's shift c plus the mean of the shifted values.
+__global__ void offset_kernel(const float* __restrict__ c, const double* __restrict__ sum_d, int64_t n, int m,
+                              double* __restrict__ a_off) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) a_off[j] = (double)c[j] + sum_d[j] / (double)n;
 }
 
 __global__ void copy_f32_kernel(const float* __restrict__ a, int m, float* __restrict__ b) {
@@ -155,7 +142,8 @@ fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n)
     if (p.sg_order < 0 || p.sg_order > 7) return fail(ctx, FKK_ERR_INVALID_ARG, "bad sg_order");
   }
   if (!(p.ratio_floor > 0.f)) return fail(ctx, FKK_ERR_INVALID_ARG, "ratio_floor must be > 0");
-  if (p.precision != FKK_PREC_BF16X3) return fail(ctx, FKK_ERR_INVALID_ARG, "unknown precision");
+  if (p.precision != FKK_PREC_BF16X3 && p.precision != FKK_PREC_BF16)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "unknown precision %d", p.precision);
   if (p.noise_alpha < 0.0 || p.noise_sigma_g < 0.0) return fail(ctx, FKK_ERR_INVALID_ARG, "negative noise parameter");
   if (p.svd != FKK_SVD_EXACT && p.svd != FKK_SVD_RANDOMIZED) return fail(ctx, FKK_ERR_INVALID_ARG, "bad svd");
   if (p.svd == FKK_SVD_RANDOMIZED) {
@@ -195,7 +183,7 @@ BasisParams basis_params(const fkk_fit_params& p, int m, int L) {
 // vectors (the layout basis_alloc carves up).
 size_t basis_block_bytes(int m, int k) {
   const size_t mk = (size_t)m * k;
-  const size_t doubles = (size_t)m + 2 * k + 2 * mk + 7 * mk;
+  const size_t doubles = (size_t)m + 2 * k + 2 * mk + 7 * mk + (size_t)m;  // ... c_ph, then a_off (m)
   return doubles * 8 + (size_t)2 * k * 8 + 64 + (size_t)m * 4 + 256;
 }
 
@@ -225,6 +213,7 @@ fkk_basis* basis_alloc(fkk_ctx* ctx, int m, int k, fkk_status* st) {
   b->v_sec_t = d; d += mk;
   b->c_amp = d; d += mk;
   b->c_ph = d; d += mk;
+  b->a_off = d; d += m;
   b->q = (int64_t*)d;
   b->nq = (int*)(b->q + 2 * k);
   b->energy = reinterpret_cast<double*>(b->nq) + 1;
@@ -412,6 +401,7 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
     FKK_COUNT_LAUNCH(); energy_kernel<<<1, 256, 0, st>>>(D.sum_d2, D.sum_d, D.c, B->f, n, m, B->energy);
   }
   FKK_COUNT_LAUNCH(); s_and_w_kernel<<<k, 256, 0, st>>>(B->lam, B->v, m, k, p.ml_lambda, B->s, B->w);
+  FKK_COUNT_LAUNCH(); offset_kernel<<<(m + 127) / 128, 128, 0, st>>>(D.c, D.sum_d, n, m, B->a_off);
   float* P = (float*)workspace(ctx, "fit_p", (size_t)n * k * 4, &s);
   if (!P) return bail(s);
   int64_t* qm = (int64_t*)workspace(ctx, "fit_qext", (size_t)2 * k * 8, &s);
@@ -449,14 +439,19 @@ fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int6
                      float* re_out, int64_t ld_out, void* stream) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  if (!B || !im_out) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null argument");
+  if (!B) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null basis");
   if (n < 0 || ld < B->m || ld_out < B->m) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: bad sizes");
   if (n == 0) return FKK_OK;
-  if (!i_cars) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null input");
+  if (!i_cars || !im_out) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: null array");
   if (B->device != ctx->device) return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_apply: basis on another device");
   FKK_TRY(bind(ctx));
   cudaStream_t st = as_stream(stream);
   fkk_status s;
+  bool handled = false;
+  FKK_TRY(launch_apply_fused(ctx, B, i_cars, n, ld, im_out, re_out, ld_out, st, &handled));
+  if (handled) return FKK_OK;
+  // strides or alignments TMA cannot address, or k > 62: projection, then
+  // the reconstruction (fp32-accurate in either precision setting)
   float* P = (float*)workspace(ctx, "apply_p", (size_t)n * B->k * 4, &s);
   if (!P) return s;
   FKK_TRY(launch_project_raw(ctx, i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, B->w, B->f, B->k, P, st));
@@ -531,6 +526,7 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
   cp(B->w, w.data(), mk * 8);
   cp(B->c_amp, c_amp, mk * 8);
   cp(B->c_ph, c_ph, mk * 8);
+  if (e == cudaSuccess) e = cudaMemset(B->a_off, 0, (size_t)m * 8);
   cp(B->i_ref, ir.data(), m * 4);
   cp(B->nq, &zero, sizeof zero);
   const double no_energy = 0.0;  // unknown for an imported basis
@@ -554,7 +550,7 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
 // basis in the layout basis_alloc defines).
 namespace {
 constexpr char kMagic[8] = {'F', 'K', 'K', 'B', 'A', 'S', 'I', 'S'};
-constexpr uint32_t kFormat = 1;
+constexpr uint32_t kFormat = 2;  // 2: the training offset of the log ratios follows C_ph
 struct FileHead {
   char magic[8];
   uint32_t version;
@@ -637,11 +633,30 @@ fkk_status fkk_basis_load(fkk_ctx* ctx, const char* path, fkk_basis** out) {
   return FKK_OK;
 }
 
+fkk_status fkk_basis_set_offset(fkk_basis* b, const double* offset, int32_t n_channels) {
+  if (!b || !offset || n_channels != b->m) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(b->pack_mu);
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FKK_ERR_CUDA;
+  if (cudaMemcpy(b->a_off, offset, (size_t)b->m * 8, cudaMemcpyHostToDevice) != cudaSuccess) return FKK_ERR_CUDA;
+  if (b->pack) {  // the packed operands carry the offset: rebuild on next use
+    cudaFree(b->pack);
+    b->pack = nullptr;
+  }
+  return FKK_OK;
+}
+
+fkk_status fkk_basis_set_precision(fkk_basis* b, int32_t precision) {
+  if (!b || (precision != FKK_PREC_BF16X3 && precision != FKK_PREC_BF16)) return FKK_ERR_INVALID_ARG;
+  b->params.precision = precision;
+  return FKK_OK;
+}
+
 void fkk_basis_free(fkk_basis* b) {
   if (!b) return;
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   cudaFree(b->block);
+  if (b->pack) cudaFree(b->pack);
   delete b;
 }
 

@@ -103,9 +103,21 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
 fkk_status launch_gather_q(fkk_ctx* ctx, const int64_t* qmax, const int64_t* qmin, int k, const float* p,
                            int64_t n_rows, int64_t* q, int* nq_dev, double* x_rows, cudaStream_t st);
 
-// Out = exp(P C_amp) sin(P C_ph) (and cos for re_out), P n x k fp32.
+// Out = exp(P C_amp) sin(P C_ph) (and cos for re_out), P n x k fp32 (the
+// tensor-core reconstruction, three bf16 products per term).
 fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
                               const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st);
+
+// ML:fKK-EC apply of a trained basis in one fused launch (projection of the
+// raw spectra and reconstruction) in the basis' precision.  *handled is false
+// and nothing is launched when TMA cannot address the arrays (row strides not
+// multiples of 4 floats, 16-byte misaligned or host arrays) or k > 62.
+fkk_status launch_apply_fused(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int64_t n, int64_t ld,
+                              float* im, float* re, int64_t ld_out, cudaStream_t st, bool* handled);
+
+// Packed operands of the fused apply, built once per basis (and again after
+// fkk_basis_set_offset).
+fkk_status apply_pack(fkk_ctx* ctx, const fkk_basis* B, cudaStream_t st);
 
 // Out = P C + 1 b^T (n x m, ld_out), C k x m fp64 row-major, b m floats or
 // null: the linear epilogue of the same tensor-core kernel (the SVD

@@ -346,6 +346,11 @@ fkk_status launch_reconstruct_tc(fkk_ctx* ctx, const float* p, int64_t n, int k,
   return recon_tc_ws(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, st, false, nullptr);
 }
 
+fkk_status launch_reconstruct(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c_amp,
+                              const double* c_ph, float* im, float* re, int64_t ld_out, cudaStream_t st) {
+  return recon_tc_ws(ctx, p, n, k, m, c_amp, c_ph, im, re, ld_out, st, false, nullptr);
+}
+
 fkk_status launch_reconstruct_linear(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, const double* c,
                                      const float* bias, float* out, int64_t ld_out, cudaStream_t st) {
   return recon_tc_ws(ctx, p, n, k, m, c, c, out, nullptr, ld_out, st, true, bias);
