@@ -424,29 +424,41 @@ fkk_status fkk_basis_load(fkk_ctx* ctx, const char* path, fkk_basis** out);
 fkk_status fkk_noise_scale(fkk_ctx* ctx, const float* mean_spectrum, int32_t n_channels, double alpha,
                            double sigma_g, double* f_out, void* stream);
 
-/* Serving of a trained basis (Sec. 2.6, Eq. ML_Unew then Eq. fKKEC).  A
- * server runs one worker thread with its own stream and its own context on
- * the basis' device (same HBM budget as ctx, workspace separate from ctx's).
- * Submitted tiles queue in order; the worker gathers consecutive tiles into
- * one batch up to its staging size (continuous batching), runs the apply
- * once and scatters the results.  Larger tiles run alone (device tiles in
- * place, host tiles in staging-sized chunks).  The basis must outlive the
- * server. */
+/* Serving of a trained basis (Sec. 2.6, Eq. ML_Unew then Eq. fKKEC) with
+ * continuous batching.  A server has its own context on the basis' device
+ * (same HBM budget as ctx, workspace separate from ctx's), a dispatcher
+ * thread and three batch slots; each slot owns a CUDA stream and device
+ * staging for `cap` spectra in and out.  cap is the tune cache's max_batch
+ * (or 65,536), reduced to what the HBM budget leaves for the three slots.
+ * Submitted requests queue in order; the dispatcher moves them into the
+ * first free slot -- consecutive host tiles gathered into one batch while
+ * their spectra fit the slot (one fused apply for all of them), a device
+ * tile alone, in place -- and enqueues the batch (copies in, apply, copies
+ * out) on the slot's stream without waiting, so up to three batches are in
+ * flight and the copies of one overlap the kernel of another.  The apply of
+ * a gathered batch is replayed from a CUDA graph captured once per slot and
+ * 1,024-spectrum bucket.  A request waits in the queue while every slot is
+ * busy (admission deferred until staging frees up).  The basis must outlive
+ * the server and keep its precision while the server runs. */
 typedef struct fkk_server fkk_server;
 typedef uint64_t fkk_req;
 
-/* tune_cache_or_null: a text file holding "max_batch=<spectra>"; when the
- * path is given but holds no entry, a short calibration of the apply at
- * batch sizes 2048, 4096, ... picks the smallest within 10% of the best
- * throughput and writes it there.  Without a path the staging size is the
- * largest power of two <= 65,536 spectra that fits the budget. */
+/* tune_cache_or_null: a text file with the lines "max_batch=<spectra>" and
+ * "stages=<0..4>" (ring depth of the fused apply, 0 = the deepest that
+ * fits).  When the path is given but lacks either entry, an autotuner times
+ * the apply at each ring depth and at batch sizes 2,048, 4,096, ..., cap,
+ * keeps the fastest depth and the smallest batch within 10 % of the best
+ * throughput, and writes both.  Errors: FKK_ERR_INVALID_ARG, FKK_ERR_CUDA,
+ * FKK_ERR_BUDGET (the budget leaves no room for 128 spectra per slot). */
 fkk_status fkk_serve_start(fkk_ctx* ctx, const fkk_basis* basis, const char* tune_cache_or_null, fkk_server** out);
 
 /* Queue a tile of n_spectra spectra (n_channels of the basis each, rows
  * contiguous) and return its id at once.  tile_on_host = 0: tile and
  * im_out are device pointers; 1: both are pinned host memory.  The buffers
  * belong to the caller and must stay valid until the request is waited.
- * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_SHUTDOWN (server stopping). */
+ * Errors: FKK_ERR_INVALID_ARG, FKK_ERR_SHUTDOWN (server stopping),
+ * FKK_ERR_BUDGET (a host tile of more spectra than a slot's staging holds:
+ * it can never be admitted; split it). */
 fkk_status fkk_serve_submit(fkk_server* server, const float* tile, int64_t n_spectra, int32_t tile_on_host,
                             float* im_out, fkk_req* out_id);
 
@@ -462,9 +474,16 @@ fkk_status fkk_serve_wait(fkk_server* server, fkk_req id, int32_t timeout_ms);
  * submit).  Any pointer may be NULL. */
 fkk_status fkk_serve_stats(fkk_server* server, double* p50_ms, double* p99_ms, double* spectra_per_s);
 
-/* Stop: queued requests complete with FKK_ERR_SHUTDOWN, a batch already
- * running finishes, threads blocked in fkk_serve_wait return, and the
- * server (its stream, context and staging) is freed. */
+/* The last (up to 1,024) completed batches, oldest first, 5 doubles each:
+ * start and end in milliseconds (CUDA events recorded on the slot's stream
+ * before its first copy and after its last, relative to the server's start),
+ * slot index, number of requests, number of spectra.  Writes at most
+ * max_rows rows to out (host) and their count to *n_rows. */
+fkk_status fkk_serve_batch_log(fkk_server* server, double* out, int32_t max_rows, int32_t* n_rows);
+
+/* Stop: queued requests complete with FKK_ERR_SHUTDOWN, batches already
+ * issued finish, threads blocked in fkk_serve_wait return, and the server
+ * (its streams, graphs, context and staging) is freed. */
 fkk_status fkk_serve_stop(fkk_server* server);
 
 /* Largest problem fkk_reconstruct_noalloc accepts in one call. */

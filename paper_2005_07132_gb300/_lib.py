@@ -79,6 +79,7 @@ SIGNATURES = {
     "fkk_serve_wait": (_I32, [_P, C.c_uint64, _I32]),
     "fkk_serve_stats": (_I32, [_P, C.POINTER(_F64), C.POINTER(_F64), C.POINTER(_F64)]),
     "fkk_serve_stop": (_I32, [_P]),
+    "fkk_serve_batch_log": (_I32, [_P, _P, _I32, C.POINTER(_I32)]),
 }
 
 
@@ -559,6 +560,18 @@ class Server:
         p50, p99, rate = _F64(), _F64(), _F64()
         lib().fkk_serve_stats(self._h, C.byref(p50), C.byref(p99), C.byref(rate))
         return {"p50_ms": p50.value, "p99_ms": p99.value, "spectra_per_s": rate.value}
+
+    def batch_log(self, max_rows: int = 1024):
+        """Completed batches (fkk_serve_batch_log): rows of start_ms, end_ms,
+        slot, requests, spectra, as a float64 numpy array."""
+        import numpy as np
+
+        out = np.zeros((max_rows, 5), np.float64)
+        n = _I32()
+        st = lib().fkk_serve_batch_log(self._h, out.ctypes.data_as(C.c_void_p), max_rows, C.byref(n))
+        if st != FKK_OK:
+            raise FkkError(st, "fkk_serve_batch_log")
+        return out[: n.value]
 
     def stop(self):
         if self._h:

@@ -515,13 +515,13 @@ __global__ void chan_consts_kernel(const float* __restrict__ i_ref, const double
   cc[64] = j < m ? (float)off[j] : 0.f;
 }
 
-size_t fused_smem(int kp1, bool x3, bool re, int* stages, uint32_t* stage_bytes, uint32_t* w_bytes) {
+size_t fused_smem(int kp1, bool x3, bool re, int want, int* stages, uint32_t* stage_bytes, uint32_t* w_bytes) {
   const uint32_t wb = (uint32_t)kp1 * 128;
   uint32_t st = kIBytes + (x3 ? 2 : 1) * wb + kConstBytes;
   st = (st + 1023) & ~1023u;
   const size_t fixed = 1024 + 2 * kPopHalf + 2 * (x3 ? 2 : 1) * kCHalf + 4 * (re ? 2 : 1) * kStg + 512;
   const size_t cap = 227 * 1024;
-  int s = kMaxStages;
+  int s = (want >= 2 && want <= kMaxStages) ? want : kMaxStages;
   while (s > 2 && fixed + (size_t)s * st > cap) --s;
   *stages = s;
   *stage_bytes = st;
@@ -600,7 +600,8 @@ fkk_status launch_apply_fused(fkk_ctx* ctx, const fkk_basis* B, const float* i_c
   a.floor_ = B->params.ratio_floor;
   a.consts = B->consts;
   a.status = ctx->d_status;
-  const size_t smem = fused_smem(a.kp1, a.x3 != 0, re != nullptr, &a.stages, &a.stage_bytes, &a.w_bytes);
+  const size_t smem =
+      fused_smem(a.kp1, a.x3 != 0, re != nullptr, ctx->apply_stages, &a.stages, &a.stage_bytes, &a.w_bytes);
   if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "apply: tile does not fit shared memory");
   CUtensorMap ti, twh, twl, tch, tcl, tim, tre;
   FKK_TRY(make_tmap_2d(ctx, &ti, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<float*>(i_cars), (uint64_t)m,

@@ -42,6 +42,9 @@ struct fkk_ctx {
   // (forked and joined with the two events; created on first use)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // ring depth of the fused apply kernel (0 = the deepest that fits; the
+  // serving autotuner sets it on its own context)
+  int apply_stages = 0;
 };
 
 namespace fkk {

@@ -3,7 +3,10 @@ the serving path (Sec. 2.6: new spectra are projected on the frozen basis
 and reconstructed with its cached coefficients).
 
 Serving runs the same kernels as fkk_apply row by row, so its outputs must
-equal fkk_apply's bit for bit, however the tiles are batched.
+equal fkk_apply's bit for bit, however the tiles are batched and whichever
+slot runs them; batches in different slots overlap on the device; the HBM
+budget bounds each slot's staging, so a host tile larger than a slot is
+refused with FKK_ERR_BUDGET and requests that find every slot busy wait.
 """
 import threading
 
@@ -16,7 +19,7 @@ from paper_2005_07132_gb300.synth import CubeSpec, make_cube
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FKK_ERR_TIMEOUT, FKK_ERR_BAD_FILE, FKK_ERR_SHUTDOWN = -4, -6, -7
+FKK_ERR_BUDGET, FKK_ERR_TIMEOUT, FKK_ERR_BAD_FILE, FKK_ERR_SHUTDOWN = -2, -4, -6, -7
 
 
 @pytest.fixture(scope="module")
@@ -122,29 +125,80 @@ def test_serve_device_and_host_tiles_equal_apply(fk, ctx, trained, tmp_path):
     srv.stop()
 
 
-def test_serve_large_host_tile_in_chunks(fk, ctx, trained, tmp_path):
+def _pinned(t):
+    return t.cpu().pin_memory()
+
+
+def test_serve_budget_defers_then_completes_and_refuses(fk, trained):
+    """A context budget of three slots of 4,096 spectra: a host tile of
+    5,000 can never be staged (FKK_ERR_BUDGET at submit); four tiles of 3,000
+    (no two fit one slot) take the three slots and the fourth waits for one
+    to free, then completes with the same output as fkk_apply."""
     cube, x, ref, basis = trained
-    cache = tmp_path / "tune.txt"
-    cache.write_text("max_batch=1000\n")  # staging of 1,000 spectra
-    srv = fk.Server(ctx, basis, tune_cache=cache)
-    big = torch.cat([x] * 3).contiguous()  # 9,216 spectra
-    want = _reference(fk, ctx, basis, big)
-    tile = big.cpu().pin_memory()
-    out = torch.empty_like(tile).pin_memory()
-    rid = srv.submit(tile, out)
-    assert srv.wait(rid, 20000) == 0
-    assert torch.equal(out.cuda(), want)
+    m = x.shape[1]
+    small = fk.Context(0, hbm_budget_bytes=3 * 2 * 4096 * m * 4 + (1 << 20))
+    srv = fk.Server(small, basis)
+    big = _pinned(torch.cat([x, x])[:5000].contiguous())
+    with pytest.raises(fk.FkkError) as e:
+        srv.submit(big, torch.empty_like(big).pin_memory())
+    assert e.value.status == FKK_ERR_BUDGET
+    tiles = [_pinned(torch.cat([x, x])[i * 700:i * 700 + 3000].contiguous()) for i in range(4)]
+    outs = [torch.empty_like(t).pin_memory() for t in tiles]
+    ids = [srv.submit(t, o) for t, o in zip(tiles, outs)]
+    for rid in ids:
+        assert srv.wait(rid, 20000) == 0
+    for t, o in zip(tiles, outs):
+        assert torch.equal(o.cuda(), _reference(fk, small, basis, t.cuda()))
+    log = srv.batch_log()
+    assert len(log) == 4 and np.all(log[:, 3] == 1) and np.all(log[:, 4] == 3000)
+    # the fourth batch was admitted only after one of the first three ended
+    assert log[3, 0] >= log[:3, 1].min()
+    srv.stop()
+    small.close()
+
+
+def test_serve_batches_overlap_and_equal_alone(fk, ctx, trained):
+    """Host tiles submitted together run as batches in different slots whose
+    event intervals intersect on the device; each result equals the tile's
+    own fkk_apply bit for bit."""
+    cube, x, ref, basis = trained
+    big = torch.cat([x] * 8).contiguous()  # 24,576 spectra per tile
+    tiles = [_pinned(torch.roll(big, i * 37, 0)) for i in range(9)]
+    outs = [torch.empty_like(t).pin_memory() for t in tiles]
+    srv = fk.Server(ctx, basis)
+    ids = [srv.submit(t, o) for t, o in zip(tiles, outs)]
+    for rid in ids:
+        assert srv.wait(rid, 30000) == 0
+    log = srv.batch_log()
+    assert len(log) >= 2
+    overlaps = sum(1 for i in range(len(log)) for j in range(i + 1, len(log))
+                   if log[i, 2] != log[j, 2] and log[i, 0] < log[j, 1] and log[j, 0] < log[i, 1])
+    assert overlaps >= 1, log
+    for t, o in zip(tiles, outs):
+        assert torch.equal(o.cuda(), _reference(fk, ctx, basis, t.cuda()))
     srv.stop()
 
 
-def test_serve_tune_cache_written(fk, ctx, trained, tmp_path):
-    _, _, _, basis = trained
+def test_serve_tune_cache_written_and_read(fk, ctx, trained, tmp_path):
+    _, x, _, basis = trained
     cache = tmp_path / "fresh.txt"
     srv = fk.Server(ctx, basis, tune_cache=cache)
     srv.stop()
     text = cache.read_text()
-    assert text.startswith("max_batch=")
-    assert 2048 <= int(text.split("=")[1]) <= 65536
+    vals = dict(line.split("=") for line in text.split())
+    assert 2048 <= int(vals["max_batch"]) <= 65536 and int(vals["stages"]) in (2, 3, 4)
+    # a cached max_batch bounds the slots: a host tile above it is refused
+    cache.write_text("max_batch=1024\nstages=2\n")
+    srv = fk.Server(ctx, basis, tune_cache=cache)
+    tile = _pinned(x[:1100].contiguous())
+    with pytest.raises(fk.FkkError) as e:
+        srv.submit(tile, torch.empty_like(tile).pin_memory())
+    assert e.value.status == FKK_ERR_BUDGET
+    ok = _pinned(x[:1024].contiguous())
+    out = torch.empty_like(ok).pin_memory()
+    assert srv.wait(srv.submit(ok, out), 20000) == 0
+    assert torch.equal(out.cuda(), _reference(fk, ctx, basis, ok.cuda()))
+    srv.stop()
 
 
 def test_serve_wait_timeout_then_complete(fk, ctx, trained):
