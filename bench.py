@@ -11,15 +11,18 @@ on the basis, reconstruction.
 
 Printed (one JSON line, rank 0): value = fKK-EC spectra/s of the whole job,
 the per-stage breakdown, the roofline of the dominant stage, the same metric
-end to end through pinned host buffers (e2e: pipelined as a stream of cubes
-runs, with the in-order figure beside it), the FP64 CPU oracle on a bounded
+end to end (e2e: fkk_fit_basis called through the C ABI on pinned host
+buffers, two contexts on alternating streams as a stream of cubes runs; the
+in-order and torch-copy figures beside it), the FP64 CPU oracle on a bounded
 sample of the same cube (cpu_baseline), the per-spectrum KK and the ML apply
-throughput on the same cube, the fit with the randomised SVD, the
-conventional workflow (with and without the SVD denoising of the raw
-spectra), serving latency and throughput, the speed-enhancement curve on the
-simulation-shaped workload, clocks sampled during the timed region, and the
-number of library kernels launched in it.  --svd randomized makes the
-randomised SVD the timed fit.
+(fp32-accurate and reduced-precision forms, with the reduced form's measured
+error at k = 20, 40, 80) on the same cube, the fit with the randomised SVD,
+the conventional workflow (with and without the SVD denoising of the raw
+spectra), serving latency and throughput under a 40 GB budget, the batched
+multi-image workload, the speed-enhancement curve on the simulation-shaped
+workload, clocks sampled during the timed region, and the number of library
+kernels launched in it.  --svd randomized makes the randomised SVD the timed
+fit.
 
 --impl reference times the oracle itself (plain FP64 numpy) as the reference
 arm: each step is an oracle fit of a bounded sample of the same workload.
@@ -56,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cube of synth.CONFIGS to fit (the benchmark workload by default; a smaller one keeps "
                          "profiler captures small)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="duration of the 50,000 spectra/s Poisson serving leg (about 2 requests per second)")
     ap.add_argument("--svd", default="exact", choices=["exact", "randomized"],
                     help="factorisation of A in the timed fit: the Gram matrix and its eigensolve, or the "
                          "randomised SVD (10 oversampling columns, 2 power iterations)")
@@ -483,30 +488,51 @@ def run_ours(args, rank, world, local):
                        "mode": "pipelined: upload of step i and download of step i-1 beside the fit (3 streams)",
                        "serial": {"value": world * n / (serial_ms / 1e3), "ms_per_step": serial_ms,
                                   "mode": "upload, fit, download in order on one stream"}}
-        # the C ABI called with the pinned host buffers themselves (the library
-        # copies them in and the output back on the fit's stream)
-        try:
-            def host_step():
-                b, _, _ = fk.fkk_fit_basis(ctx, xh, refh, prm, im_out=oh, stream=st)
-                return b
+        # the public call on the pinned host buffers themselves: the library
+        # copies the cube in and the result out on the call's stream.  In
+        # order on one stream, then as a stream of cubes runs: two contexts
+        # (one workspace each) on two streams, step i on context i % 2, so
+        # the upload of one cube overlaps the fit and download of the other.
+        outs_h = [torch.empty_like(xh).pin_memory() for _ in range(2)]
+        ctxs = [ctx, fk.Context(local)]
+        streams = [st, torch.cuda.Stream()]
 
-            for _ in range(2):
-                bases.append(host_step())
-            torch.cuda.synchronize()
-            e0.record(st)
-            for _ in range(args.steps):
-                bases.append(host_step())
-            e1.record(st)
-            torch.cuda.synchronize()
-            host_ms = e0.elapsed_time(e1) / args.steps
-            line["e2e"]["c_abi_host_buffers"] = {
-                "value": world * n / (host_ms / 1e3), "ms_per_step": host_ms,
-                "mode": "fkk_fit_basis on the pinned host cube and output, in order on one stream"}
-        except Exception as exc:  # reported, not fatal: the other figures stand
-            line["e2e"]["c_abi_host_buffers"] = {"error": str(exc)[:200]}
+        def host_step(i):
+            j = i % 2
+            b, _, _ = fk.fkk_fit_basis(ctxs[j], xh, refh, prm, im_out=outs_h[j], stream=streams[j])
+            return b
+
+        for i in range(2):
+            bases.append(host_step(i))
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            bases.append(host_step(0))
+        e1.record(st)
+        torch.cuda.synchronize()
+        host_serial_ms = e0.elapsed_time(e1) / args.steps
         for b in bases:
             b.close()
         bases.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            bases.append(host_step(i))
+        torch.cuda.synchronize()
+        host_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        for b in bases:
+            b.close()
+        bases.clear()
+        ctxs[1].close()
+        torch_piped = line["e2e"]
+        line["e2e"] = {"value": world * n / (host_ms / 1e3), "unit": "spectra/s",
+                       "h2d_bytes_per_step": int(xh.numel() * 4 + refh.numel() * 4),
+                       "d2h_bytes_per_step": int(oh.numel() * 4), "ms_per_step": host_ms,
+                       "mode": "fkk_fit_basis (C ABI) on the pinned host cube and output; two contexts on "
+                               "alternating streams, host wall clock over the steps",
+                       "c_abi_in_order": {"value": world * n / (host_serial_ms / 1e3), "ms_per_step": host_serial_ms,
+                                          "mode": "the same call, one context, one stream"},
+                       "torch_copies": torch_piped}
 
         # ---- per-spectrum KK and ML apply on the same cube ----
         def timed(fn, reps=5):
@@ -519,14 +545,33 @@ def run_ours(args, rank, world, local):
             torch.cuda.synchronize()
             return e0.elapsed_time(e1) / reps
 
+        hbm_peak = (pk or {}).get("hbm_gbs", 6800.0)
         kk_ms = timed(lambda: fk.kk_per_spectrum(ctx, x, ref, im_out=out, stream=st))
-        basis = step()
-        ap_ms = timed(lambda: fk.fkk_apply(ctx, basis, x, im_out=out, stream=st))
-        basis.close()
         line["kk_per_spectrum"] = {"value": n / (kk_ms / 1e3), "unit": "spectra/s", "ms": kk_ms,
-                                   "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9}
-        line["apply"] = {"value": n / (ap_ms / 1e3), "unit": "spectra/s", "ms": ap_ms,
-                         "hbm_gbs": 8.0 * n * m / (ap_ms / 1e3) / 1e9}
+                                   "hbm_gbs": 8.0 * n * m / (kk_ms / 1e3) / 1e9,
+                                   "hbm_frac": 8.0 * n * m / (kk_ms / 1e3) / 1e9 / hbm_peak}
+        # ML apply (Sec. 2.6) with the fitted basis, in both precisions; the
+        # reduced form's error is measured against the fp32-accurate form on
+        # the whole cube (the tests bound both against the fp64 oracle)
+        line["apply"] = {}
+        out2 = torch.empty_like(x)
+        for kb in (20, 40, 80):
+            bp = fk.fit_params(k=kb, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g)
+            basis, _, _ = fk.fkk_fit_basis(ctx, x, ref, bp, stream=st)
+            ent = {}
+            for prec, name in ((fk.PREC_BF16X3, "bf16x3"), (fk.PREC_BF16, "bf16")):
+                basis.set_precision(prec)
+                o = out if prec == fk.PREC_BF16X3 else out2
+                a_ms = timed(lambda: fk.fkk_apply(ctx, basis, x, im_out=o, stream=st))
+                ent[name] = {"value": n / (a_ms / 1e3), "unit": "spectra/s", "ms": a_ms,
+                             "hbm_gbs": 8.0 * n * m / (a_ms / 1e3) / 1e9,
+                             "hbm_frac": 8.0 * n * m / (a_ms / 1e3) / 1e9 / hbm_peak}
+            torch.cuda.synchronize()
+            ent["bf16_rel_l2_vs_bf16x3"] = float(torch.linalg.vector_norm(out2 - out) / torch.linalg.vector_norm(out))
+            ent["fused"] = kb <= 62
+            line["apply"][f"k{kb}"] = ent
+            basis.close()
+        del out2
         # the same fit with the randomised SVD (Sec. 5) in place of the Gram
         # matrix and its eigensolve, at 2 and 1 power iterations
         line["randomized_svd"] = {}
@@ -552,7 +597,7 @@ def run_ours(args, rank, world, local):
         dn_ms = timed(lambda: fk.conventional_per_spectrum(ctx, x, ref, dn_prm, im_out=out, stream=st), reps=3)
         line["conventional"]["with_svd_denoise"] = {"value": n / (dn_ms / 1e3), "unit": "spectra/s", "ms": dn_ms,
                                                     "denoise_k": 6}
-        line["serve"] = serve_leg(fk, ctx)
+        line["serve"] = serve_leg(fk, local, args.serve_seconds)
         line["simulation"] = sim_leg(fk, ctx, st)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(cube)
@@ -619,73 +664,89 @@ def sim_leg(fk, ctx, st, reps=3):
     return res
 
 
-def serve_leg(fk, ctx, seconds=1.0):
-    """Serving of a trained basis (train 400 x 500 x 1,000, k = 40): tiles
-    of U{1,000..50,000} spectra cut from a new image of the same scene, in
-    pinned host memory, arriving as a Poisson process at 50,000 spectra/s,
-    then all at once (saturation).  Latency is submit -> completion."""
+def serve_leg(fk, device, seconds_50k=20.0):
+    """Serving of a trained basis (train 400 x 500 x 1,000, k = 40) under a
+    40 GB HBM budget: tiles of U{1,000..50,000} spectra cut from a new image
+    of the same scene, in pinned host memory, arriving as a Poisson process
+    at 50,000 spectra/s (for `seconds_50k` seconds), at half the saturation
+    rate (1,000 requests), and all at once (saturation, 1,000 requests).
+    Latency is submit -> completion; the batch log gives the share of batches
+    whose device interval overlaps a batch of another slot."""
     import numpy as np
     import torch
 
     from paper_2005_07132_gb300.synth import CONFIGS, Scene, make_cube
 
+    budget = 40 << 30
+    sctx = fk.Context(device, hbm_budget_bytes=budget)
     spec = CONFIGS["train400x500_m1000"]
     scene = Scene.from_spec(spec)
     train = make_cube(spec, image=0, scene=scene)
     new = make_cube(spec, image=1, scene=scene)
     x = torch.from_numpy(train.i_cars).cuda()
     ref = torch.from_numpy(train.i_ref).cuda()
-    basis, _, _ = fk.fkk_fit_basis(ctx, x, ref, fk.fit_params(k=K_BASIS))
+    basis, _, _ = fk.fkk_fit_basis(sctx, x, ref, fk.fit_params(k=K_BASIS))
     del x
     pool = torch.from_numpy(new.i_cars).pin_memory()
     outp = torch.empty_like(pool).pin_memory()
     n_pool = pool.shape[0]
     rng = np.random.default_rng(4)
 
-    def tiles(total):
-        out, pos, used = [], 0, 0
-        while used < total:
+    def tiles(count):
+        out, pos = [], 0
+        for _ in range(count):
             t = int(rng.integers(1000, 50001))
             if pos + t > n_pool:
                 pos = 0
             out.append((pos, t))
             pos += t
-            used += t
         return out
 
-    res = {"tile_sizes": "U{1000..50000}", "input": "pinned host", "train": "400x500x1000, k=40"}
+    def overlap_share(log):
+        if len(log) < 2:
+            return 0.0
+        hit = 0
+        for i in range(len(log)):
+            if any(log[j, 2] != log[i, 2] and log[i, 0] < log[j, 1] and log[j, 0] < log[i, 1]
+                   for j in range(len(log)) if j != i):
+                hit += 1
+        return hit / len(log)
 
-    def poisson(rate, secs):
-        # Poisson arrivals at `rate` spectra/s for about `secs` seconds
-        srv = fk.Server(ctx, basis)
-        plan = tiles(int(rate * secs))
-        gaps = rng.exponential([t / rate for _, t in plan])
+    def run(rate, count):
+        """count requests arriving as a Poisson process at `rate` spectra/s
+        (rate None: all at once)."""
+        srv = fk.Server(sctx, basis)
+        plan = tiles(count)
         ids = []
-        due = time.perf_counter()
-        for (pos, t), g in zip(plan, gaps):
-            due += g
-            while time.perf_counter() < due:
-                pass
+        t0 = time.perf_counter()
+        due = t0
+        for pos, t in plan:
+            if rate:
+                due += rng.exponential(t / rate)
+                while time.perf_counter() < due:
+                    pass
             ids.append(srv.submit(pool[pos:pos + t], outp[pos:pos + t]))
         for rid in ids:
             srv.wait(rid)
+        wall = time.perf_counter() - t0
         st = srv.stats()
         st["requests"] = len(ids)
+        st["spectra"] = int(sum(t for _, t in plan))
+        st["wall_s"] = wall
+        st["batch_overlap_share"] = overlap_share(srv.batch_log())
         srv.stop()
         return st
 
-    res["poisson_50k_per_s"] = poisson(50_000, 6.0 * seconds)
-    res["poisson_5M_per_s"] = poisson(5_000_000, 1.0 * seconds)
-    # saturation: everything queued at once
-    srv = fk.Server(ctx, basis)
-    plan = tiles(int(600_000))
-    ids = [srv.submit(pool[pos:pos + t], outp[pos:pos + t]) for pos, t in plan]
-    for rid in ids:
-        srv.wait(rid)
-    res["saturation"] = srv.stats()
-    res["saturation"]["requests"] = len(ids)
-    srv.stop()
+    res = {"tile_sizes": "U{1000..50000}", "input": "pinned host", "train": "400x500x1000, k=40",
+           "hbm_budget_bytes": budget, "slots": 3}
+    res["saturation"] = run(None, 1000)
+    sat = res["saturation"]["spectra_per_s"]
+    res["poisson_half_saturation"] = run(0.5 * sat, 1000)
+    res["poisson_half_saturation"]["arrival_rate"] = 0.5 * sat
+    n50 = max(4, int(50_000 * seconds_50k / 25_500))
+    res["poisson_50k_per_s"] = run(50_000, n50)
     basis.close()
+    sctx.close()
     return res
 
 

@@ -233,8 +233,11 @@ typedef struct fkk_basis fkk_basis;
  * i_cars, i_ref, f_or_null and the outputs may be device or host memory
  * (pinned or pageable): host inputs are copied into the context's workspace
  * on `stream` before the transform and host outputs copied back after the
- * reconstruction (pinned: asynchronously on `stream`; pageable: before the
- * call returns).  im_out and re_out must be of the same kind. */
+ * reconstruction (pinned: asynchronously on `stream`, so pinned inputs must
+ * stay unchanged and pinned outputs unread until `stream` has reached the
+ * end of the call; pageable: before the call returns).  im_out and re_out
+ * must be of the same kind.  Fits on different streams run concurrently
+ * only with one context per stream (each context owns its workspace). */
 fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, int32_t n_channels, int64_t ld,
                          const float* i_ref, const float* f_or_null, const fkk_fit_params* params,
                          fkk_basis** out_basis, float* im_out_or_null, float* re_out_or_null, int64_t ld_out,

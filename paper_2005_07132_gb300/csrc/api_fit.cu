@@ -285,8 +285,11 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
     if (is_host_ptr(i_cars)) {
       float* d = (float*)workspace(ctx, "fit_host_x", (size_t)n * m * 4, &sh);
       if (!d) return sh;
-      FKK_CUDA(ctx, cudaMemcpy2DAsync(d, (size_t)m * 4, i_cars, (size_t)ld * 4, (size_t)m * 4, (size_t)n,
-                                      cudaMemcpyHostToDevice, st));
+      if (ld == m)  // packed rows: one linear copy (a pitched copy moves row by row)
+        FKK_CUDA(ctx, cudaMemcpyAsync(d, i_cars, (size_t)n * m * 4, cudaMemcpyHostToDevice, st));
+      else
+        FKK_CUDA(ctx, cudaMemcpy2DAsync(d, (size_t)m * 4, i_cars, (size_t)ld * 4, (size_t)m * 4, (size_t)n,
+                                        cudaMemcpyHostToDevice, st));
       i_cars = d;
       ld = m;
     }
@@ -420,14 +423,15 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
   stage_mark(ctx, 5, st);
   if (im_out) {
     if ((s = launch_reconstruct(ctx, P, n, k, m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st))) return bail(s);
-    if (im_host &&
-        (s = cuda_check(ctx, cudaMemcpy2DAsync(im_host, (size_t)ld_host * 4, im_out, (size_t)m * 4, (size_t)m * 4,
-                                               (size_t)n, cudaMemcpyDeviceToHost, st), "copy Im to host")))
-      return bail(s);
-    if (re_host &&
-        (s = cuda_check(ctx, cudaMemcpy2DAsync(re_host, (size_t)ld_host * 4, re_out, (size_t)m * 4, (size_t)m * 4,
-                                               (size_t)n, cudaMemcpyDeviceToHost, st), "copy Re to host")))
-      return bail(s);
+    // device-to-host: one linear copy when the host rows are packed
+    auto to_host = [&](float* dst, const float* src, const char* what) {
+      if (ld_host == m)
+        return cuda_check(ctx, cudaMemcpyAsync(dst, src, (size_t)n * m * 4, cudaMemcpyDeviceToHost, st), what);
+      return cuda_check(ctx, cudaMemcpy2DAsync(dst, (size_t)ld_host * 4, src, (size_t)m * 4, (size_t)m * 4, (size_t)n,
+                                               cudaMemcpyDeviceToHost, st), what);
+    };
+    if (im_host && (s = to_host(im_host, im_out, "copy Im to host"))) return bail(s);
+    if (re_host && (s = to_host(re_host, re_out, "copy Re to host"))) return bail(s);
   }
   stage_mark(ctx, 6, st);
   if ((s = cuda_check(ctx, cudaGetLastError(), "fkk_fit_basis"))) return bail(s);
