@@ -598,6 +598,7 @@ def run_ours(args, rank, world, local):
         line["conventional"]["with_svd_denoise"] = {"value": n / (dn_ms / 1e3), "unit": "spectra/s", "ms": dn_ms,
                                                     "denoise_k": 6}
         line["serve"] = serve_leg(fk, local, args.serve_seconds)
+        line["multi_image"] = multi_image_leg(fk, ctx, st)
         line["simulation"] = sim_leg(fk, ctx, st)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(cube)
@@ -661,6 +662,59 @@ def sim_leg(fk, ctx, st, reps=3):
             pt["mean_rss"] = {"fkk_ec": rss_f, "conventional": rss_c, "null": float(np.mean(np.sum(truth**2, 1)))}
         res["points"].append(pt)
         del x, ref, out, out2
+    return res
+
+
+def multi_image_leg(fk, ctx, st, reps=3):
+    """The batched multi-image workload: 16 independent cubes (their own
+    scenes; sides 128..1,024, M in {512, 878, 1,000, 1,600}, k in
+    {10, 20, 40, 80}, drawn by the seeded stream 1005), each tiled from a
+    128 x 128 draw of its scene, fitted and reconstructed end to end by one
+    fkk_fit_many call (two worker lanes), beside the same fits one after the
+    other on one stream."""
+    import torch
+
+    from paper_2005_07132_gb300.synth import make_tiled_cube, multi_image_specs
+
+    jobs = []
+    total = 0
+    for spec, k in multi_image_specs():
+        cube = make_tiled_cube(spec)
+        x = torch.from_numpy(cube.i_cars).cuda()
+        ref = torch.from_numpy(cube.i_ref).cuda()
+        jobs.append((x, ref, fk.fit_params(k=k), torch.empty_like(x)))
+        total += x.shape[0]
+        del cube
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for b in fk.fkk_fit_many(ctx, jobs, stream=st):  # warm-up (workspaces, lanes)
+        b.close()
+    torch.cuda.synchronize()
+    made = []
+    e0.record(st)
+    for _ in range(reps):
+        made += fk.fkk_fit_many(ctx, jobs, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    many_ms = e0.elapsed_time(e1) / reps
+    for b in made:
+        b.close()
+    made.clear()
+    e0.record(st)
+    for x, ref, prm, out in jobs:
+        made.append(fk.fkk_fit_basis(ctx, x, ref, prm, im_out=out, stream=st)[0])
+    e1.record(st)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    for b in made:
+        b.close()
+    status, _ = ctx.sync_status()
+    res = {"cubes": len(jobs), "spectra": total, "bytes_in": int(sum(j[0].numel() * 4 for j in jobs)),
+           "value": total / (many_ms / 1e3), "unit": "spectra/s", "ms": many_ms,
+           "sequential": {"value": total / (seq_ms / 1e3), "ms": seq_ms},
+           "device_status": int(status), "input": "each cube tiled from a 128 x 128 draw of its own scene"}
+    del jobs
+    torch.cuda.empty_cache()
     return res
 
 

@@ -87,6 +87,15 @@ size_t fkk_workspace_bytes(const fkk_ctx* ctx);
  * FKK_ERR_NOT_CONVERGED), else FKK_OK.  `clamped` may be NULL. */
 fkk_status fkk_sync_status(fkk_ctx* ctx, void* stream, int64_t* clamped);
 
+/* Test of the device-side timeout path: the next eigensolve on ctx (in
+ * fkk_fit_basis, fkk_eig_topk or conventional_per_spectrum's denoising)
+ * waits, in the first column exchange of its tridiagonal reduction, for a
+ * tag that no step publishes, with a bound of 2^14 polls instead of 2^20.
+ * The wait runs out, the reduction records FKK_ERR_TIMEOUT and every CTA
+ * returns; the eigenpairs of that call are undefined, fkk_sync_status
+ * reports FKK_ERR_TIMEOUT, and the context stays usable.  One-shot. */
+fkk_status fkk_test_stall_next_eigensolve(fkk_ctx* ctx);
+
 /* Per-stage timing of fkk_fit_basis: 0 off; 1 on: each fit records CUDA
  * events on its stream at the boundaries of six stages: 0 transform (log
  * ratio, split, channel sums), 1 Gram, 2 eigensolve, 3 projection and
@@ -242,6 +251,33 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n_spectra, i
                          const float* i_ref, const float* f_or_null, const fkk_fit_params* params,
                          fkk_basis** out_basis, float* im_out_or_null, float* re_out_or_null, int64_t ld_out,
                          void* stream);
+
+/* One cube of fkk_fit_many: the arguments of fkk_fit_basis for one image
+ * (arrays device or host as there), with its own parameters. */
+typedef struct {
+  const float* i_cars;
+  int64_t n_spectra;
+  int32_t n_channels;
+  int64_t ld;
+  const float* i_ref;
+  const float* f_or_null;
+  float* im_out;   /* may be NULL (no reconstruction) */
+  float* re_out;   /* may be NULL */
+  int64_t ld_out;
+  fkk_fit_params params;
+} fkk_cube_job;
+
+/* Fit many independent cubes (images of different sizes, channel counts and
+ * k; Fig. 1(b) on each) in one call: out_bases[i] receives job i's basis,
+ * exactly as fkk_fit_basis would produce it.  The jobs run, largest first,
+ * on two worker lanes -- contexts of their own with their own streams and
+ * workspaces (each capped at half of ctx's budget), kept on ctx for later
+ * calls -- so the stages of different cubes overlap on the device.  The
+ * lanes start after the work already on `stream`; `stream` waits for both
+ * at the end, and the lanes' device status (clamp counts, eigensolver
+ * failures) is added to ctx's (fkk_sync_status).  On an argument or CUDA
+ * error every basis made so far is freed and out_bases is all NULL. */
+fkk_status fkk_fit_many(fkk_ctx* ctx, int32_t n_jobs, const fkk_cube_job* jobs, fkk_basis** out_bases, void* stream);
 
 /* ML:fKK-EC (Sec. 2.6): U_new S = A_new V diag(s^2/(s^2+ml_lambda)) with the
  * basis's f, I_ref and ratio floor (Eq. ML_Unew), then Eq. fKKEC with the
@@ -501,10 +537,11 @@ fkk_status fkk_serve_stop(fkk_server* server);
  * must not hit the implicit device synchronisation of cudaMalloc/cudaFree.
  * fkk_reconstruct keeps its packed operands in the context's grow-only
  * workspace, which is (re)allocated the first time a larger batch arrives;
- * this entry point packs them instead into two fixed arrays compiled into
- * the library (10 MiB of static device memory per device: bf16 hi/lo
- * copies of P for up to FKK_NOALLOC_MAX_SPECTRA rows at K = 128, and of the
- * interleaved coefficients for up to FKK_NOALLOC_MAX_CHANNELS channels).
+ * this entry point packs them instead into four fixed arrays compiled into
+ * the library (bf16 hi and lo parts of P for up to FKK_NOALLOC_MAX_SPECTRA
+ * rows at K = 128, and of the interleaved coefficients for up to
+ * FKK_NOALLOC_MAX_CHANNELS channels; 10 MiB of static device memory per
+ * device).
  *
  * Limits: 0 <= n_spectra <= FKK_NOALLOC_MAX_SPECTRA, 1 <= k <= 80,
  * 1 <= m <= FKK_NOALLOC_MAX_CHANNELS, ld_out >= m; anything larger returns

@@ -44,6 +44,7 @@ SIGNATURES = {
     "fkk_version": (C.c_char_p, []),
     "fkk_launch_count": (C.c_uint64, []),
     "fkk_set_timing": (_I32, [_P, _I32]),
+    "fkk_test_stall_next_eigensolve": (_I32, [_P]),
     "fkk_stage_ms": (_I32, [_P, C.POINTER(C.c_float), _I32]),
     "fkk_eig_phase_cycles": (_I32, [_P, C.POINTER(_I64), _I32]),
     "fkk_create": (_I32, [C.POINTER(_P), _I32, _SZ]),
@@ -59,6 +60,7 @@ SIGNATURES = {
     "fkk_fit_params_size": (_SZ, []),
     "fkk_fit_basis": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P, C.POINTER(_P), _P, _P, _I64, _P]),
     "fkk_apply": (_I32, [_P, _P, _P, _I64, _I64, _P, _P, _I64, _P]),
+    "fkk_fit_many": (_I32, [_P, _I32, _P, _P, _P]),
     "fkk_basis_free": (None, [_P]),
     "fkk_basis_set_precision": (_I32, [_P, _I32]),
     "fkk_basis_set_offset": (_I32, [_P, _P, _I32]),
@@ -96,6 +98,15 @@ class FitParams(C.Structure):
         ("svd", C.c_int32), ("rsvd_oversample", C.c_int32), ("rsvd_power_iters", C.c_int32),
         ("rsvd_seed", C.c_uint64),
         ("denoise_k", C.c_int32),
+    ]
+
+
+class CubeJob(C.Structure):
+    """Mirror of fkk_cube_job (include/fkk.h)."""
+
+    _fields_ = [
+        ("i_cars", _P), ("n_spectra", _I64), ("n_channels", _I32), ("ld", _I64), ("i_ref", _P),
+        ("f_or_null", _P), ("im_out", _P), ("re_out", _P), ("ld_out", _I64), ("params", FitParams),
     ]
 
 
@@ -181,6 +192,11 @@ class Context:
     def check(self, st: int, where: str):
         if st != FKK_OK:
             raise FkkError(st, where, lib().fkk_last_error(self._h).decode())
+
+    def stall_next_eigensolve(self):
+        """Test knob: the next eigensolve's first exchange wait runs out
+        (fkk_test_stall_next_eigensolve)."""
+        self.check(lib().fkk_test_stall_next_eigensolve(self._h), "fkk_test_stall_next_eigensolve")
 
     def last_error(self) -> str:
         return lib().fkk_last_error(self._h).decode()
@@ -379,6 +395,32 @@ def fkk_fit_basis(ctx: Context, i_cars, i_ref, params: FitParams, f=None, im_out
     return Basis(h, ctx), im_out, re_out
 
 
+def fkk_fit_many(ctx: Context, cubes, stream=None):
+    """Fit many cubes in one call (C: fkk_fit_many).  `cubes` is a list of
+    (i_cars, i_ref, params, im_out) with im_out None for no reconstruction;
+    returns the list of Basis objects."""
+    jobs = (CubeJob * len(cubes))()
+    keep = []
+    for j, (x, ref, prm, out) in zip(jobs, cubes):
+        _check_2d(x, "i_cars")
+        if out is not None:
+            _check_2d(out, "im_out")
+            if tuple(out.shape) != tuple(x.shape):
+                raise ValueError("im_out must have the shape of i_cars")
+        j.i_cars, j.n_spectra, j.n_channels, j.ld = _ptr(x), x.shape[0], x.shape[1], x.stride(0)
+        j.i_ref = _ptr(ref)
+        j.f_or_null = None
+        j.im_out = _ptr(out) if out is not None else None
+        j.re_out = None
+        j.ld_out = out.stride(0) if out is not None else x.shape[1]
+        j.params = prm
+        keep.append((x, ref, out))
+    hs = (_P * len(cubes))()
+    st = lib().fkk_fit_many(ctx.handle, len(cubes), C.cast(jobs, _P), C.cast(hs, _P), _stream(stream))
+    ctx.check(st, "fkk_fit_many")
+    return [Basis(h, ctx) for h in hs]
+
+
 def fkk_apply(ctx: Context, basis: Basis, i_cars, im_out=None, re_out=None, stream=None):
     """ML:fKK-EC on new spectra (C: fkk_apply).  Returns im_out (re_out)."""
     import torch
@@ -463,15 +505,43 @@ def fkk_basis_math(ctx: Context, v, params: FitParams, x_rows=None, f=None, stre
     return c_amp, c_ph
 
 
+def _check_reconstruct(p, c_amp, c_ph, im_out, re_out):
+    """Shapes, dtypes and devices of the reconstruction's arguments, checked
+    before the C call (a wrong one would make the kernels read or write out of
+    bounds): p float32 (n, k); c_amp, c_ph contiguous float64 (k, m) on p's
+    device; im_out / re_out float32 views of at least (n, m) on that device
+    with unit column stride and one common row stride."""
+    import torch
+
+    if p.dim() != 2 or p.dtype != torch.float32 or not p.is_contiguous():
+        raise ValueError("p must be a contiguous float32 (n, k) tensor")
+    n, k = p.shape
+    for t, nm in ((c_amp, "c_amp"), (c_ph, "c_ph")):
+        if t.dim() != 2 or t.dtype != torch.float64 or not t.is_contiguous() or t.shape[0] != k:
+            raise ValueError(f"{nm} must be a contiguous float64 (k, m) tensor with k = {k}")
+        if t.device != p.device:
+            raise ValueError(f"{nm} must be on p's device")
+    m = c_amp.shape[1]
+    if tuple(c_ph.shape) != (k, m):
+        raise ValueError("c_amp and c_ph must have the same shape")
+    for t, nm in ((im_out, "im_out"), (re_out, "re_out")):
+        if t is None:
+            continue
+        if t.dim() != 2 or t.dtype != torch.float32 or t.device != p.device or t.stride(1) != 1:
+            raise ValueError(f"{nm} must be a float32 2-D tensor with unit column stride on p's device")
+        if t.shape[0] < n or t.shape[1] < m or t.stride(0) < m:
+            raise ValueError(f"{nm} must hold at least ({n}, {m})")
+    if im_out is not None and re_out is not None and im_out.stride(0) != re_out.stride(0):
+        raise ValueError("im_out and re_out must share the row stride")
+    return n, k, m
+
+
 def fkk_reconstruct(ctx: Context, p, c_amp, c_ph, im_out=None, re_out=None, stream=None):
     import torch
 
-    for t, nm in ((p, "p"), (c_amp, "c_amp"), (c_ph, "c_ph")):
-        _dense(t, nm)
-    n, k = p.shape
-    m = c_amp.shape[1]
     if im_out is None:
-        im_out = torch.empty((n, m), dtype=torch.float32, device=p.device)
+        im_out = torch.empty((p.shape[0], c_amp.shape[1]), dtype=torch.float32, device=p.device)
+    n, k, m = _check_reconstruct(p, c_amp, c_ph, im_out, re_out)
     st = lib().fkk_reconstruct(ctx.handle, _ptr(p), n, k, m, _ptr(c_amp), _ptr(c_ph), _ptr(im_out), _ptr(re_out),
                                im_out.stride(0), _stream(stream))
     ctx.check(st, "fkk_reconstruct")
@@ -488,10 +558,9 @@ def fkk_reconstruct_noalloc(ctx: Context, p, c_amp, c_ph, im_out, re_out=None, s
         st = lib().fkk_reconstruct_noalloc(ctx.handle, None, 0, 1, 1, None, None, None, None, 1, _stream(stream))
         ctx.check(st, "fkk_reconstruct_noalloc")
         return im_out
-    for t, nm in ((p, "p"), (c_amp, "c_amp"), (c_ph, "c_ph")):
-        _dense(t, nm)
-    n, k = p.shape
-    m = c_amp.shape[1]
+    if im_out is None:
+        raise ValueError("fkk_reconstruct_noalloc needs im_out")
+    n, k, m = _check_reconstruct(p, c_amp, c_ph, im_out, re_out)
     st = lib().fkk_reconstruct_noalloc(ctx.handle, _ptr(p), n, k, m, _ptr(c_amp), _ptr(c_ph), _ptr(im_out),
                                        _ptr(re_out), im_out.stride(0), _stream(stream))
     ctx.check(st, "fkk_reconstruct_noalloc")

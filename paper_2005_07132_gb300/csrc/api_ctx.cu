@@ -127,10 +127,23 @@ fkk_status fkk_create(fkk_ctx** out, int32_t device, size_t hbm_budget_bytes) {
   return FKK_OK;
 }
 
+fkk_status fkk_test_stall_next_eigensolve(fkk_ctx* ctx) {
+  if (!ctx) return FKK_ERR_INVALID_ARG;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->stall_next_eig = 1;
+  return FKK_OK;
+}
+
 fkk_status fkk_destroy(fkk_ctx* ctx) {
   if (!ctx) return FKK_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->lane_done[i]) cudaEventDestroy(ctx->lane_done[i]);
+    if (ctx->lane_st[i]) cudaStreamDestroy(ctx->lane_st[i]);
+    if (ctx->lane_ctx[i]) fkk_destroy(ctx->lane_ctx[i]);
+  }
+  if (ctx->lane_start) cudaEventDestroy(ctx->lane_start);
   for (auto& kv : ctx->ws)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
   for (auto& e : ctx->ev)

@@ -454,11 +454,14 @@ fkk_status fkk_apply(fkk_ctx* ctx, const fkk_basis* B, const float* i_cars, int6
   bool handled = false;
   FKK_TRY(launch_apply_fused(ctx, B, i_cars, n, ld, im_out, re_out, ld_out, st, &handled));
   if (handled) return FKK_OK;
-  // strides or alignments TMA cannot address, or k > 62: projection, then
-  // the reconstruction (fp32-accurate in either precision setting)
+  // strides or alignments TMA cannot address, or k > 62: the fit's
+  // transform (log ratios as bf16 hi / lo, channel-major), its tensor-core
+  // projection and the reconstruction (fp32-accurate in either precision)
   float* P = (float*)workspace(ctx, "apply_p", (size_t)n * B->k * 4, &s);
   if (!P) return s;
-  FKK_TRY(launch_project_raw(ctx, i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, B->w, B->f, B->k, P, st));
+  DtLayout D;
+  FKK_TRY(launch_transform(ctx, i_cars, n, B->m, ld, B->i_ref, B->params.ratio_floor, D, st));
+  FKK_TRY(launch_project(ctx, D, B->w, B->f, B->k, P, nullptr, nullptr, st));
   return launch_reconstruct(ctx, P, n, B->k, B->m, B->c_amp, B->c_ph, im_out, re_out, ld_out, st);
 }
 

@@ -45,6 +45,14 @@ struct fkk_ctx {
   // ring depth of the fused apply kernel (0 = the deepest that fits; the
   // serving autotuner sets it on its own context)
   int apply_stages = 0;
+  // fkk_test_stall_next_eigensolve: the next eigensolve's first exchange
+  // waits for a tag that is never published (its bounded wait runs out)
+  int stall_next_eig = 0;
+  // worker lanes of fkk_fit_many (own contexts and streams), created on first use
+  fkk_ctx* lane_ctx[2] = {};
+  cudaStream_t lane_st[2] = {};
+  cudaEvent_t lane_done[2] = {};
+  cudaEvent_t lane_start = nullptr;
 };
 
 namespace fkk {

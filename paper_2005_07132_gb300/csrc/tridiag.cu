@@ -92,7 +92,7 @@ constexpr int kMaxPer = 4;  // vector entries per vector thread: m <= kMaxPer * 
 // the abort flag; returns false then, or when another CTA has aborted.
 __device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i0, int stride, int lo, int m,
                                               unsigned tag, unsigned long long (&wv)[kMaxPer], int* abort_flag,
-                                              long long* status) {
+                                              long long* status, unsigned limit) {
   unsigned pending = 0;
 #pragma unroll
   for (int r = 0; r < kMaxPer; ++r) {
@@ -111,7 +111,7 @@ __device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i
     if (!pending) return true;
     if ((++it & 63u) == 0) {
       if (*(volatile int*)abort_flag) return false;
-      if (it > (1u << 20)) {
+      if (it > limit) {
         atomicExch(abort_flag, 1);
         record_error(status, kErrTimeout);
         return false;
@@ -149,6 +149,8 @@ struct TridArgs {
   unsigned* bar;
   int* abort_flag;
   long long* status;
+  unsigned wait_limit;  // polls before an exchange wait gives up (FKK_ERR_TIMEOUT)
+  int stall;            // test knob: step 0 waits for tag 0, which no step publishes
 };
 
 template <bool kSmem>
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
   for (int j = 0; j < nsteps; ++j) {
     if (c_last < j + 2) break;  // nothing of this CTA's is read from step j on
     const int buf = j & 1, nxt = buf ^ 1;
-    const unsigned want = step_tag(j);
+    const unsigned want = (a.stall && j == 0) ? 0u : step_tag(j);
     const unsigned long long* pb = a.pbuf + (size_t)buf * m;
     const unsigned long long* cb = a.cbuf + (size_t)buf * m;
     const bool last = (j + 1 > m - 3);
@@ -312,8 +314,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         }
       }
       unsigned long long wp[kMaxPer], wcb[kMaxPer];
-      ok = gather_tagged(pb, tid, kVecThreads, j + 1, m, want, wp, a.abort_flag, a.status) &&
-           gather_tagged(cb, tid, kVecThreads, j + 1, m, want, wcb, a.abort_flag, a.status);
+      ok = gather_tagged(pb, tid, kVecThreads, j + 1, m, want, wp, a.abort_flag, a.status, a.wait_limit) &&
+           gather_tagged(cb, tid, kVecThreads, j + 1, m, want, wcb, a.abort_flag, a.status, a.wait_limit);
 #pragma unroll
       for (int r = 0; r < kMaxPer; ++r) {
         const int i = tid + r * kVecThreads;
@@ -1223,8 +1225,12 @@ fkk_status launch_eig_topk(fkk_ctx* ctx, const double* g, int m, int k, double* 
       cycles = (long long*)workspace(ctx, "eig_phase_cycles", 8 * sizeof(long long), &s);
       if (!cycles) return s;
     }
-    TridArgs ta{g, m, ncol_max, work, pbuf, cbuf, dd, ee, tau, u, scr + 40, ex_dev, cycles, scr, (int*)(scr + 16),
-                ctx->d_status};
+    // the test knob of fkk_test_stall_next_eigensolve: one eigensolve whose
+    // first exchange waits for a tag nobody publishes, with a short bound
+    const int stall = ctx->stall_next_eig;
+    ctx->stall_next_eig = 0;
+    TridArgs ta{g,     m,         ncol_max,      work,          pbuf,   cbuf,  dd, ee, tau, u, scr + 40, ex_dev,
+                cycles, scr,      (int*)(scr + 16), ctx->d_status, stall ? (1u << 14) : (1u << 20), stall};
     void* args[] = {&ta};
     const void* fn = in_smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
     FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tr));

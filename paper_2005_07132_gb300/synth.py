@@ -81,6 +81,27 @@ CONFIGS = {
 }
 
 
+# The batched multi-image workload: 16 independent cubes, each its own scene
+# (species, NRB, surrogate) with sides, channel counts and k drawn from the
+# lists below by the seeded stream 1005; cube i has seed 1005 + i.
+MULTI_SIDES = (128, 256, 512, 1024)
+MULTI_CHANNELS = (512, 878, 1000, 1600)
+MULTI_K = (10, 20, 40, 80)
+
+
+def multi_image_specs(count: int = 16, seed: int = 1005):
+    """(CubeSpec, k) of each cube of the multi-image workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.choice(MULTI_SIDES))
+        m = int(rng.choice(MULTI_CHANNELS))
+        k = int(rng.choice(MULTI_K))
+        species = int(rng.integers(8, 31))
+        out.append((CubeSpec(side, side, m, species, "gauss", 50.0, seed=seed + i), k))
+    return out
+
+
 @dataclass
 class Scene:
     """Species, NRB and surrogate shared by every image drawn from one spec."""
@@ -252,6 +273,21 @@ def make_cube(spec: CubeSpec, *, image: int = 0, height: int | None = None,
         scene.set_noise(_mean_clean(scene, conc))
     i_cars = _render(scene, conc, image, None, spec.noise != "none")
     return Cube(scene, conc, i_cars, scene.i_ref.astype(np.float32), image)
+
+
+def make_tiled_cube(spec: CubeSpec, base: int = 128) -> Cube:
+    """A cube of the spec's size made by repeating a base x base draw of its
+    scene over the image (the full-size multi-image cubes, whose fit cost
+    does not depend on the repetition, without drawing up to 10^6 spectra
+    each); spec.height and spec.width must be multiples of base."""
+    if spec.height % base or spec.width % base:
+        raise ValueError("cube sides must be multiples of the base tile")
+    c = make_cube(spec, height=base, width=base)
+    ry, rx = spec.height // base, spec.width // base
+    img = c.i_cars.reshape(base, base, -1)
+    full = np.tile(img, (ry, rx, 1)).reshape(spec.height * spec.width, -1)
+    conc = np.tile(c.conc.reshape(base, base, -1), (ry, rx, 1)).reshape(spec.height * spec.width, -1)
+    return Cube(c.scene, conc, np.ascontiguousarray(full), c.i_ref, c.image)
 
 
 def tile_stream(scene: Scene, sizes, first_image: int = 1):

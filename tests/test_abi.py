@@ -4,6 +4,8 @@ that needs no GPU."""
 import ctypes as C
 import subprocess
 
+import pytest
+
 from abi_util import built_lib, declared_functions
 
 
@@ -85,3 +87,30 @@ def test_fit_params_defaults():
     assert abs(p.ratio_floor - 1e-6) < 1e-12
     assert (p.k_max, p.rank_eps, p.svd, p.rsvd_oversample, p.rsvd_power_iters, p.rsvd_seed) == (80, 0.0, 0, 10, 2, 0)
     assert p.denoise_k == 0
+
+
+def test_reconstruct_wrappers_reject_bad_arguments():
+    """The binding checks shapes, dtypes and strides of the reconstruction's
+    arrays before the C call (CPU tensors suffice: nothing reaches a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_2005_07132_gb300._lib import _check_reconstruct
+
+    p = torch.zeros((10, 4), dtype=torch.float32)
+    ca = torch.zeros((4, 7), dtype=torch.float64)
+    cp = torch.zeros((4, 7), dtype=torch.float64)
+    im = torch.zeros((10, 7), dtype=torch.float32)
+    assert _check_reconstruct(p, ca, cp, im, None) == (10, 4, 7)
+    bad = [
+        (p.double(), ca, cp, im, None),                    # p not float32
+        (p, ca.float(), cp, im, None),                     # coefficients not float64
+        (p, ca[:3], cp, im, None),                         # k mismatch
+        (p, ca, cp[:, :6], im, None),                      # c_ph shape
+        (p, ca, cp, im[:9], None),                         # too few output rows
+        (p, ca, cp, im[:, :6], None),                      # too few output channels
+        (p, ca, cp, im.double(), None),                    # output dtype
+        (p, ca, cp, im, torch.zeros((10, 8))[:, :7]),      # Re with another row stride
+        (p, ca.t().contiguous().t(), cp, im, None),        # non-contiguous coefficients
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            _check_reconstruct(*args)

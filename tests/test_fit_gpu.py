@@ -7,24 +7,33 @@ Tolerances and where they come from:
     terms per factor (three products), relative error <= 3 * 2^-17 of
     |d_i d_j|, fp32 accumulation in TMEM and fp64 across splits; centring
     makes |d| ~30x smaller than |a|, so |dG| <= 2e-6 max|G|.
-  * eigenpairs: fp64 deflation of the dominant pair, fp32 Jacobi, fp64
-    Rayleigh-Ritz refinement; eigenvalues to 1e-8 lambda_1, residual
-    ||G V - V L|| <= 1e-6 ||G||.
+  * eigenpairs: Householder tridiagonalisation, Sturm multisection and
+    twisted-factorisation eigenvectors in double-word (about 48-bit)
+    arithmetic, back-transformed and orthonormalised; eigenvalues to
+    1e-12 lambda_1, ||V^T V - I|| <= 1e-12, ||G V - V L|| <= 1e-12 ||G||.
   * projection: fp32 accumulation of bf16-pair inputs, |dP| <= 5e-6 max|P|;
     argmax / argmin rows equal to the oracle's wherever the oracle's margin
     between the two largest (smallest) values exceeds that bound.
   * basis math: fp64 on both sides; rel <= 1e-9.
   * reconstruction / end to end: relative L2 of Im{K} <= 1e-4 (the FP32-path
-    bound); the sub-sampled rows q must be identical end to end.
+    bound); the sub-sampled rows q must be identical end to end; and per
+    element |dIm| <= 2e-4 max|Im| + 1e-4 |Im| (PER_ELEM), so that an error
+    concentrated in a few channels cannot hide inside the norm: a relative
+    perturbation of the Gram matrix moves the output by about 500 times as
+    much at k = 40 (the noise-floor singular values at the cut are 4e-5 to
+    1e-3 apart, relatively), and the Gram's own error is about 1e-7.
 """
 import numpy as np
 import pytest
 
 import oracle as O
-from gpu_util import rel_l2
+from gpu_util import elementwise_ratio, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+
+PER_ELEM = (2e-4, 1e-4)
 
 
 @pytest.fixture(scope="module")
@@ -232,6 +241,7 @@ def test_fit_end_to_end_img64(fk, ctx, cube1, pec, sec):
     st, _ = ctx.sync_status()
     assert st == 0
     assert rel_l2(im.cpu().numpy(), res["im"]) <= 1e-4
+    assert elementwise_ratio(im.cpu().numpy(), res["im"], *PER_ELEM) <= 1.0
     if pec:
         np.testing.assert_array_equal(basis.get("q").astype(np.int64), res["q"])
     # the dominant singular value is unique; noise-floor ones move with the
@@ -249,8 +259,9 @@ def test_fit_precision_by_k(fk, ctx, cube1, k):
     st, _ = ctx.sync_status()
     assert st == 0
     err = rel_l2(im.cpu().numpy(), res["im"])
-    print(f"precision k={k}: rel-L2(Im) = {err:.3e}")
-    assert err <= 1e-4
+    worst = elementwise_ratio(im.cpu().numpy(), res["im"], *PER_ELEM)
+    print(f"precision k={k}: rel-L2(Im) = {err:.3e}, worst element / bound {worst:.3f}")
+    assert err <= 1e-4 and worst <= 1.0
     basis.close()
 
 
@@ -281,6 +292,7 @@ def test_apply_with_oracle_basis(fk, ctx, cube1):
     basis = fk.fkk_basis_from_arrays(ctx, prm, b_o.f, b_o.s, b_o.V, b_o.c_amp, b_o.c_ph, b_o.i_ref)
     im = fk.fkk_apply(ctx, basis, _dev(new.i_cars))
     assert rel_l2(im.cpu().numpy(), im_o) <= 1e-4
+    assert elementwise_ratio(im.cpu().numpy(), im_o, *PER_ELEM) <= 1.0
 
 
 def test_apply_on_training_equals_fit(fk, ctx, cube1):
@@ -317,6 +329,9 @@ def test_fit_full_size_703026x1000_sampled(fk, ctx):
     assert st == 0
     got = im[torch.from_numpy(rows).cuda()].cpu().numpy()
     assert rel_l2(got, res["im"]) <= 1e-4
+    worst = elementwise_ratio(got, res["im"], *PER_ELEM)
+    print(f"full size: worst element / bound {worst:.3f}")
+    assert worst <= 1.0
     np.testing.assert_array_equal(basis.get("q").astype(np.int64), res["q"])
 
 

@@ -19,6 +19,27 @@ def test_philox_matches_numpy(key):
         assert tuple(int(v) for v in raw[4 * b: 4 * b + 4]) == O.philox4x64((b + 1, 0, 0, 0), key)
 
 
+@pytest.mark.parametrize("seed", [0, 3, 2**64 - 7])
+def test_philox_normals_mapping_by_hand(seed):
+    """The mapping of the normals, computed here from NumPy's Philox words
+    and the textbook Box-Muller formula: NumPy increments its 256-bit counter
+    before each block, so a counter of all ones yields the block at counter
+    (0, 0, 0, 0), then (1, 0, 0, 0); entries 2b and 2b + 1 are
+    sqrt(-2 ln u1) (cos, sin)(2 pi u2) with u = (w >> 11 + 1/2) 2^-53 of
+    words 0 and 1 of block b."""
+    ones = np.full(4, 2**64 - 1, dtype=np.uint64)
+    bg = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=ones)
+    raw = [int(v) for v in bg.random_raw(8)]
+    want = []
+    for b in range(2):
+        w0, w1 = raw[4 * b], raw[4 * b + 1]
+        u1 = ((w0 >> 11) + 0.5) / 2.0**53
+        u2 = ((w1 >> 11) + 0.5) / 2.0**53
+        r = (-2.0 * np.log(u1)) ** 0.5
+        want += [r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)]
+    np.testing.assert_allclose(O.philox_normals(4, seed), want, rtol=1e-15, atol=1e-15)
+
+
 def test_philox_normals_are_standard_normal():
     z = O.philox_normals(200_001, seed=9)
     assert z.shape == (200_001,)
