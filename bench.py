@@ -61,6 +61,10 @@ def parse():
                          "profiler captures small)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="duration of the 50,000 spectra/s Poisson serving leg (about 2 requests per second)")
+    ap.add_argument("--profile", default=None, choices=["apply", "apply_bf16", "kk"],
+                    help="instead of the benchmark: run one operation three times on a synthetic cube of "
+                         "--profile-spectra spectra x 1,000 channels (a small case for a profiler capture)")
+    ap.add_argument("--profile-spectra", type=int, default=65536)
     ap.add_argument("--svd", default="exact", choices=["exact", "randomized"],
                     help="factorisation of A in the timed fit: the Gram matrix and its eigensolve, or the "
                          "randomised SVD (10 oversampling columns, 2 power iterations)")
@@ -804,8 +808,44 @@ def serve_leg(fk, device, seconds_50k=20.0):
     return res
 
 
+def profile_case(args):
+    """One operation, three times, on the first --profile-spectra spectra of
+    the 703,026 x 1,000 workload (apply: with a k = 40 basis fitted on its
+    first 20,000 spectra)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2005_07132_gb300 as fk
+    from paper_2005_07132_gb300.synth import CONFIGS, make_cube
+
+    spec = CONFIGS[WORKLOAD]
+    cube = make_cube(spec)
+    n = min(args.profile_spectra, cube.i_cars.shape[0])
+    ctx = fk.Context(0)
+    x = torch.from_numpy(cube.i_cars[:n]).cuda()
+    ref = torch.from_numpy(cube.i_ref).cuda()
+    out = torch.empty_like(x)
+    if args.profile == "kk":
+        run = lambda: fk.kk_per_spectrum(ctx, x, ref, im_out=out)
+    else:
+        train = torch.from_numpy(cube.i_cars[:20000]).cuda()
+        basis, _, _ = fk.fkk_fit_basis(ctx, train, ref, fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha,
+                                                                       noise_sigma_g=cube.sigma_g), reconstruct=False)
+        basis.set_precision(fk.PREC_BF16 if args.profile == "apply_bf16" else fk.PREC_BF16X3)
+        run = lambda: fk.fkk_apply(ctx, basis, x, im_out=out)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "n_spectra": n, "status": ctx.sync_status()[0]}))
+
+
 def main():
     args = parse()
+    if args.profile:
+        profile_case(args)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -1,5 +1,6 @@
-// Per-spectrum KK (Eq. KCARS with the surrogate reference of Eq. K) with one
-// warp per pair of spectra and the length-L transform held in registers.
+// Per-spectrum KK (Eq. KCARS with the surrogate reference of Eq. K) with the
+// length-L transform held in registers: one warp per pair of spectra for
+// L = 1,024, two warps per pair for L = 2,048 (kk_pair_kernel below).
 //
 // As in the shared-memory kernel, two real spectra share one complex FFT
 // (z = a0 + i a1; the Hilbert multiplier -i sgn(m) maps it to H{a0} + i H{a1}).
@@ -68,6 +69,12 @@ __device__ __forceinline__ void issue_pair(const KKWarpArgs& p, int64_t pr, floa
   }
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // slot of the 16-byte (PER = 2) or 8-byte (PER = 1) unit (row, c), c < 32
 template <int PER>
 __device__ __forceinline__ int slot(int row, int c) {
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
   if (pr < npairs) issue_pair(p, pr, stage0, lane);
   cp_commit();
   int clamped = 0;
-  const float invL = 1.0f / (float)L;
+  constexpr float kL2eL = 1.4426950408889634f * (float)L;
   for (; pr < npairs; pr += nwarps) {
     const int64_t nx = pr + nwarps;
     float* st = stage0 + sbuf * 2 * p.mpad;
@@ -119,21 +126,26 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
     __syncwarp();
     const int64_t n0 = 2 * pr;
     const bool has1 = n0 + 1 < p.n;
+    // a / L = (ln 2 / 2L) log2(max(I / I_ref, floor)) of both spectra, in
+    // place (the 1/L of the inverse transform is folded in here, exactly:
+    // L is a power of two)
     float* a0 = st;
     float* a1 = st + p.mpad;
-    // a = 1/2 ln(max(I / I_ref, floor)), in place
-    for (int j = lane; j < M; j += 32) {
-      const float r = inv_ref[j];
-      float x0 = a0[j] * r;
-      if (!(x0 >= p.floor_)) { x0 = p.floor_; ++clamped; }
-      a0[j] = 0.34657359027997264f * __log2f(x0);  // (ln 2 / 2) log2
-      float v1 = 0.f;
-      if (has1) {
-        float x1 = a1[j] * r;
-        if (!(x1 >= p.floor_)) { x1 = p.floor_; ++clamped; }
-        v1 = 0.34657359027997264f * __log2f(x1);
+    {
+      const float cl = 0.34657359027997264f / (float)L;
+      for (int j = lane; j < M; j += 32) {
+        const float r = inv_ref[j];
+        const float x0 = a0[j] * r;
+        clamped += !(x0 >= p.floor_);
+        a0[j] = cl * __log2f(fmaxf(x0, p.floor_));  // fmaxf takes the floor for NaN
+        float v1 = 0.f;
+        if (has1) {
+          const float x1 = a1[j] * r;
+          clamped += !(x1 >= p.floor_);
+          v1 = cl * __log2f(fmaxf(x1, p.floor_));
+        }
+        a1[j] = v1;
       }
-      a1[j] = v1;
     }
     __syncwarp();
     float2 x[R];
@@ -224,7 +236,7 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
         x[c] = xbuf[u];
       }
     });
-    rf::fft_dif<R, +1>(x);  // x[i] = L h[lane + 32 bitrev(i)]
+    rf::fft_dif<R, +1>(x);  // x[i] = h[lane + 32 bitrev(i)] (the input carried 1/L)
     // outputs: Im = e^a sin(phi), Re = e^a cos(phi) (or phi itself)
     float* im0 = p.im + n0 * p.ld_out;
     float* im1 = im0 + p.ld_out;
@@ -233,16 +245,17 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
       constexpr int n2 = rf::bitrev(i, LB);
       const int j = lane + 32 * n2 - left;
       if ((unsigned)j < (unsigned)M) {
-        const float ph0 = x[i].x * invL, ph1 = x[i].y * invL;
+        const float ph0 = x[i].x, ph1 = x[i].y;
         if (kPhase) {
           im0[j] = ph0;
           if (has1) im1[j] = ph1;
         } else {
-          const float e0 = exp2f(1.4426950408889634f * a0[j]);
+          // e^a = 2^(a log2(e)); the stored value is a / L
+          const float e0 = ex2_approx(kL2eL * a0[j]);
           im0[j] = e0 * __sinf(ph0);
           if (p.re) p.re[n0 * p.ld_out + j] = e0 * __cosf(ph0);
           if (has1) {
-            const float e1 = exp2f(1.4426950408889634f * a1[j]);
+            const float e1 = ex2_approx(kL2eL * a1[j]);
             im1[j] = e1 * __sinf(ph1);
             if (p.re) p.re[(n0 + 1) * p.ld_out + j] = e1 * __cosf(ph1);
           }
@@ -255,6 +268,211 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
   for (int o = 16; o > 0; o >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, o);
   if (lane == 0 && clamped)
     atomicAdd(reinterpret_cast<unsigned long long*>(p.status + 1), (unsigned long long)clamped);
+}
+
+// ---------------------------------------------------------------------------
+// Pad length 2,048 with two warps per pair of spectra (64 threads, 32 complex
+// values each): n = t + 64 n2 (thread t, register n2), k = k2 + 32 k1.
+//   1. 32-point DFT over n2 in registers; twiddle w_2048^(t k2);
+//   2. transpose through the group's shared buffer so that thread
+//      (k2 = t / 2, h = t % 2) holds the 32 values n1 = 2 j + h;
+//   3. 32-point DFT over j, then the radix-2 step of the 64-point DFT over
+//      n1 between the lane pair (h = 0, 1) with one shuffle per value:
+//      X[k2 + 32 (k1' + 32 q)] = U0[k1'] + (-1)^q w_64^k1' U1[k1'], lane h
+//      keeping q = h;
+// the inverse runs the same steps backwards.  Twiddles and the exchange use
+// the same XOR-swizzled [k2][n1] layout, conflict-free for both patterns.
+__device__ __forceinline__ int xslot(int k2, int n1) { return k2 * 64 + (n1 ^ (2 * (k2 & 7))); }
+
+__device__ __forceinline__ void group_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 w) {  // a * conj(w)
+  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+
+template <bool kPhase>
+__global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
+  constexpr int L = 2048;
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = wib >> 1, ngrp = blockDim.x >> 6;
+  const int t = threadIdx.x & 63;      // thread of the pair group
+  const int h = t & 1, k2r = t >> 1;   // reader role after the transpose
+  const int bar_id = 1 + grp;
+  // layout: twiddles (2,048 float2, swizzled) | 1/I_ref (mpad) | per group: xbuf (2,048 float2), stage[2] (2 mpad)
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float* inv_ref = reinterpret_cast<float*>(tw + L);
+  float2* gbase = reinterpret_cast<float2*>(inv_ref + p.mpad);
+  const size_t per_grp_f2 = (size_t)L + 2 * (size_t)p.mpad;
+  float2* xbuf = gbase + grp * per_grp_f2;
+  float* stage0 = reinterpret_cast<float*>(xbuf + L);
+  const int M = p.m;
+  const int left = (L - M) / 2;
+
+  for (int e = threadIdx.x; e < L; e += blockDim.x) {
+    const int n1 = e & 63, k2 = e >> 6;
+    float sv, cv;
+    sincospif(-2.0f * (float)(n1 * k2) / (float)L, &sv, &cv);
+    tw[xslot(k2, n1)] = make_float2(cv, sv);
+  }
+  for (int j = threadIdx.x; j < M; j += blockDim.x) inv_ref[j] = 1.0f / p.i_ref[j];
+  __syncthreads();
+
+  const int64_t npairs = (p.n + 1) / 2;
+  const int64_t ngroups = (int64_t)gridDim.x * ngrp;
+  int64_t pr = (int64_t)blockIdx.x * ngrp + grp;
+  int sbuf = 0;
+  const int myrow = wib & 1;  // each warp of the group stages one of the two rows
+  auto issue = [&](int64_t q, float* st) {
+    const int64_t row = 2 * q + myrow;
+    if (row >= p.n) return;
+    const float* src = p.i_cars + row * p.ld;
+    float* dst = st + myrow * p.mpad;
+    int j0 = 0;
+    if (p.vec16) {
+      const int nv = M >> 2;
+      for (int v = lane; v < nv; v += 32) cp_async16(dst + 4 * v, src + 4 * v);
+      j0 = nv << 2;
+    }
+    for (int j = j0 + lane; j < M; j += 32) cp_async4(dst + j, src + j);
+  };
+  if (pr < npairs) issue(pr, stage0);
+  cp_commit();
+  int clamped = 0;
+  constexpr float kL2eL = 1.4426950408889634f * (float)L;
+  const float cl = 0.34657359027997264f / (float)L;
+  for (; pr < npairs; pr += ngroups) {
+    const int64_t nx = pr + ngroups;
+    float* st = stage0 + sbuf * 2 * p.mpad;
+    if (nx < npairs) issue(nx, stage0 + (sbuf ^ 1) * 2 * p.mpad);
+    cp_commit();
+    cp_wait1();
+    group_bar(bar_id);  // both rows staged
+    const int64_t n0 = 2 * pr;
+    const bool has1 = n0 + 1 < p.n;
+    float* a0 = st;
+    float* a1 = st + p.mpad;
+    // a / L in place (see kk_warp_kernel); each thread of the group a share
+    for (int j = t; j < M; j += 64) {
+      const float r = inv_ref[j];
+      const float x0 = a0[j] * r;
+      clamped += !(x0 >= p.floor_);
+      a0[j] = cl * __log2f(fmaxf(x0, p.floor_));
+      float v1 = 0.f;
+      if (has1) {
+        const float x1 = a1[j] * r;
+        clamped += !(x1 >= p.floor_);
+        v1 = cl * __log2f(fmaxf(x1, p.floor_));
+      }
+      a1[j] = v1;
+    }
+    group_bar(bar_id);
+    float2 x[32];
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int n2 = decltype(q)::value;
+      const int c = min(max(t + 64 * n2 - left, 0), M - 1);
+      x[n2] = make_float2(a0[c], a1[c]);
+    });
+    // ---- forward ----
+    rf::fft_dif<32, -1>(x);  // x[i] = Y[t][bitrev(i)]
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      constexpr int k2 = rf::bitrev(i, 5);
+      const int u = xslot(k2, t);
+      xbuf[u] = cmulf(x[i], tw[u]);
+    });
+    group_bar(bar_id);
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int j = decltype(q)::value;
+      x[j] = xbuf[xslot(k2r, 2 * j + h)];
+    });
+    rf::fft_dif<32, -1>(x);  // x[i] = U_h[k1' = bitrev(i)]
+    // radix-2 step across the lane pair, then -i sgn(k); k = k2 + 32 (k1' + 32 h)
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      constexpr int k1 = rf::bitrev(i, 5);
+      const float2 tu = rf::twiddle<-1, k1, 64>(x[i]);
+      const float2 v = h ? tu : x[i];
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
+      float2 X = h ? rf::csub(o, v) : rf::cadd(v, o);  // X_h[k1']
+      const bool edge = (k1 == 0) && (k2r == 0);       // DC (h = 0) or Nyquist (h = 1)
+      X = edge ? make_float2(0.f, 0.f) : (h ? make_float2(-X.y, X.x) : make_float2(X.y, -X.x));
+      x[i] = X;
+    });
+    // ---- inverse: the radix-2 step back, U'_h = (X0 + (-1)^h X1) w_64^(-h k1')
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      constexpr int k1 = rf::bitrev(i, 5);
+      const float2 X = x[i];
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, X.x, 1), __shfl_xor_sync(0xffffffffu, X.y, 1));
+      const float2 v = h ? rf::csub(o, X) : rf::cadd(X, o);
+      x[i] = h ? rf::twiddle<+1, k1, 64>(v) : v;
+    });
+    rf::fft_dit<32, +1>(x);  // x[j]: n1 = 2 j + h
+    group_bar(bar_id);       // every thread has read its transposed values
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int j = decltype(q)::value;
+      const int u = xslot(k2r, 2 * j + h);
+      xbuf[u] = cmulf_conj(x[j], tw[u]);
+    });
+    group_bar(bar_id);
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int k2 = decltype(q)::value;
+      x[k2] = xbuf[xslot(k2, t)];
+    });
+    rf::fft_dif<32, +1>(x);  // x[i] = h[t + 64 bitrev(i)]
+    float* im0 = p.im + n0 * p.ld_out;
+    float* im1 = im0 + p.ld_out;
+    rf::static_for<0, 32>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      constexpr int n2 = rf::bitrev(i, 5);
+      const int j = t + 64 * n2 - left;
+      if ((unsigned)j < (unsigned)M) {
+        const float ph0 = x[i].x, ph1 = x[i].y;
+        if (kPhase) {
+          im0[j] = ph0;
+          if (has1) im1[j] = ph1;
+        } else {
+          const float e0 = ex2_approx(kL2eL * a0[j]);
+          im0[j] = e0 * __sinf(ph0);
+          if (p.re) p.re[n0 * p.ld_out + j] = e0 * __cosf(ph0);
+          if (has1) {
+            const float e1 = ex2_approx(kL2eL * a1[j]);
+            im1[j] = e1 * __sinf(ph1);
+            if (p.re) p.re[(n0 + 1) * p.ld_out + j] = e1 * __cosf(ph1);
+          }
+        }
+      }
+    });
+    group_bar(bar_id);  // staging and exchange buffers are rewritten next
+    sbuf ^= 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, o);
+  if (lane == 0 && clamped)
+    atomicAdd(reinterpret_cast<unsigned long long*>(p.status + 1), (unsigned long long)clamped);
+}
+
+template <bool kPhase>
+fkk_status launch_pair(fkk_ctx* ctx, const KKWarpArgs& a, cudaStream_t st) {
+  const size_t fixed = sizeof(float2) * 2048 + sizeof(float) * (size_t)a.mpad;
+  const size_t pg = sizeof(float2) * (2048 + 2 * (size_t)a.mpad);
+  const size_t cap = 227 * 1024;
+  int groups = 6;
+  while (groups > 1 && fixed + groups * pg > cap) --groups;
+  const size_t smem = fixed + groups * pg;
+  if (smem > cap) return fail(ctx, FKK_ERR_INVALID_ARG, "kk: %d channels need %zu B of shared memory", a.m, smem);
+  auto fn = kk_pair_kernel<kPhase>;
+  FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t npairs = (a.n + 1) / 2;
+  int64_t grid = (npairs + groups - 1) / groups;
+  grid = std::min<int64_t>(grid, ctx->sm_count);
+  if (grid < 1) grid = 1;
+  FKK_COUNT_LAUNCH();
+  fn<<<(unsigned)grid, groups * 64, smem, st>>>(a);
+  return cuda_check(ctx, cudaGetLastError(), "kk_pair_kernel launch");
 }
 
 template <int R>
@@ -309,7 +527,7 @@ fkk_status launch_kk_warp(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, i
   a.status = ctx->d_status;
   a.vec16 = ((reinterpret_cast<uintptr_t>(i_cars) & 15) == 0) && (ld % 4 == 0);
   *handled = true;
-  if (L == 2048) return phase ? launch_r<64, true>(ctx, a, st) : launch_r<64, false>(ctx, a, st);
+  if (L == 2048) return phase ? launch_pair<true>(ctx, a, st) : launch_pair<false>(ctx, a, st);
   return phase ? launch_r<32, true>(ctx, a, st) : launch_r<32, false>(ctx, a, st);
 }
 
