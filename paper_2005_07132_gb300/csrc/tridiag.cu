@@ -550,6 +550,7 @@ __device__ __forceinline__ void sturm_count2(const df* ds, const df* eb, int m, 
     pq1.l.y = 0.f;
   }
   int cx = pq1.h.x < 0.f, cy = pq1.h.y < 0.f;
+#pragma unroll 4
   for (int i = 1; i < m; ++i) {
     const dw2::df2 d2 = dw2::splat(ds[i]), e2 = dw2::splat(eb[i]);
     dw2::df2 pq = dw2::sub(dw2::mul(dw2::sub(d2, xy), pq1), dw2::mul(e2, pq2));
@@ -581,6 +582,7 @@ __device__ __forceinline__ void sturm_count2_f32(const df* ds, const df* eb, int
   if (p1.x == 0.f) p1.x = -0x1p-60f;
   if (p1.y == 0.f) p1.y = -0x1p-60f;
   int cx = p1.x < 0.f, cy = p1.y < 0.f;
+#pragma unroll 4
   for (int i = 1; i < m; ++i) {
     const float d = ds[i].h, e = eb[i].h;
     float2 p = __ffma2_rn(__fadd2_rn(make_float2(d, d), nxy), p1, __fmul2_rn(make_float2(-e, -e), p2));
@@ -737,6 +739,7 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
     df x = dw::sub(ds[0], ls);
     if (fabsf(x.h) < tiny) x = dw::make(-tiny);
     dp[0] = x;
+#pragma unroll 4
     for (int i = 1; i < m; ++i) {
       x = dw::sub(dw::sub(ds[i], ls), dw::div(eb[i], x));
       if (fabsf(x.h) < tiny) x = dw::make(-tiny);
@@ -746,6 +749,7 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
     df x = dw::sub(ds[m - 1], ls);
     if (fabsf(x.h) < tiny) x = dw::make(-tiny);
     dm[m - 1] = x;
+#pragma unroll 4
     for (int i = m - 2; i >= 0; --i) {
       x = dw::sub(dw::sub(ds[i], ls), dw::div(eb[i + 1], x));
       if (fabsf(x.h) < tiny) x = dw::make(-tiny);
@@ -827,6 +831,7 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
     ez[r] = 0;
     df x = dw::make(1.f);
     int ex = 0;
+#pragma unroll 4
     for (int i = r - 1; i >= 0; --i) {
       if (ex > -100000) chain_step(dp[i], x, ex);
       z[i] = ex > -100000 ? x : dw::make(0.f);
@@ -835,6 +840,7 @@ __global__ void __launch_bounds__(32) tri_vec_kernel(const df* __restrict__ d, c
   } else if (lane == 1) {
     df x = dw::make(1.f);
     int ex = 0;
+#pragma unroll 4
     for (int i = r + 1; i < m; ++i) {
       if (ex > -100000) chain_step(dm[i], x, ex);
       z[i] = ex > -100000 ? x : dw::make(0.f);
