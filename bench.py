@@ -61,7 +61,7 @@ def parse():
                          "profiler captures small)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="duration of the 50,000 spectra/s Poisson serving leg (about 2 requests per second)")
-    ap.add_argument("--profile", default=None, choices=["apply", "apply_bf16", "kk"],
+    ap.add_argument("--profile", default=None, choices=["fit", "apply", "apply_bf16", "kk"],
                     help="instead of the benchmark: run one operation three times on a synthetic cube of "
                          "--profile-spectra spectra x 1,000 channels (a small case for a profiler capture)")
     ap.add_argument("--profile-spectra", type=int, default=65536)
@@ -810,8 +810,9 @@ def serve_leg(fk, device, seconds_50k=20.0):
 
 def profile_case(args):
     """One operation, three times, on the first --profile-spectra spectra of
-    the 703,026 x 1,000 workload (apply: with a k = 40 basis fitted on its
-    first 20,000 spectra)."""
+    the 703,026 x 1,000 workload: the fit (k = 40, PEC + SEC, with the
+    reconstruction), the per-spectrum KK, or the apply with a k = 40 basis
+    fitted on its first 20,000 spectra."""
     import torch
 
     import __graft_entry__
@@ -829,6 +830,9 @@ def profile_case(args):
     out = torch.empty_like(x)
     if args.profile == "kk":
         run = lambda: fk.kk_per_spectrum(ctx, x, ref, im_out=out)
+    elif args.profile == "fit":
+        params = fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha, noise_sigma_g=cube.sigma_g)
+        run = lambda: fk.fkk_fit_basis(ctx, x, ref, params, im_out=out)[0].close()
     else:
         train = torch.from_numpy(cube.i_cars[:20000]).cuda()
         basis, _, _ = fk.fkk_fit_basis(ctx, train, ref, fk.fit_params(k=K_BASIS, noise_alpha=cube.alpha,
