@@ -569,10 +569,12 @@ def run_ours(args, rank, world, local):
                 a_ms = timed(lambda: fk.fkk_apply(ctx, basis, x, im_out=o, stream=st))
                 ent[name] = {"value": n / (a_ms / 1e3), "unit": "spectra/s", "ms": a_ms,
                              "hbm_gbs": 8.0 * n * m / (a_ms / 1e3) / 1e9,
-                             "hbm_frac": 8.0 * n * m / (a_ms / 1e3) / 1e9 / hbm_peak}
+                             "hbm_frac": 8.0 * n * m / (a_ms / 1e3) / 1e9 / hbm_peak,
+                             # one persistent kernel (else projection + reconstruction): the split
+                             # form up to k = 62, the single-product form up to k = 80
+                             "fused": kb <= 62 or prec == fk.PREC_BF16}
             torch.cuda.synchronize()
             ent["bf16_rel_l2_vs_bf16x3"] = float(torch.linalg.vector_norm(out2 - out) / torch.linalg.vector_norm(out))
-            ent["fused"] = kb <= 62
             line["apply"][f"k{kb}"] = ent
             basis.close()
         del out2

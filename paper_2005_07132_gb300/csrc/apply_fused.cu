@@ -42,23 +42,25 @@ namespace {
 constexpr int kTM = 128;      // spectra per row tile (TMEM lanes)
 constexpr int kCh = 64;       // channels per projection chunk
 constexpr int kNT = 64;       // interleaved output columns per reconstruction tile (32 channels)
-constexpr int kKp = 64;       // K storage of the P and coefficient operands (one 128-byte atom)
+constexpr int kKp = 64;       // K per 128-byte atom of the P and coefficient operands (one or two atoms)
 constexpr int kThreads = 512;  // warps 0-3 control, 4-11 transform, 12-15 epilogue
 constexpr int kTW = 8;         // transform warps
 constexpr uint32_t kConstBytes = 2 * 64 * 4;  // per chunk: 1 / I_ref, offset (64 channels each)
 constexpr int kD2 = 4;        // reconstruction accumulators
 constexpr uint32_t kIBytes = kTM * kCh * 4;   // one fp32 I chunk (two boxes)
 constexpr uint32_t kStg = 32 * 32 * 4;        // one 32 x 32 fp32 staging tile
-constexpr uint32_t kPopHalf = kTM * kKp * 2;  // P operand, one plane
-constexpr uint32_t kCHalf = kNT * kKp * 2;    // coefficient tile, one plane
-constexpr uint32_t kTmemCols = 512;           // D1 [0,64) [64,128); D2 128 + 64 b
+constexpr uint32_t kPopAtom = kTM * kKp * 2;  // P operand, one K atom of one plane
+constexpr uint32_t kCAtom = kNT * kKp * 2;    // coefficient tile, one K atom of one plane
+constexpr uint32_t kTmemCols = 512;           // D1 at d * 64 katoms; D2 at 128 katoms + 64 b
 constexpr int kMaxStages = 4;
 
 struct FusedArgs {
   int64_t n;
   int m;
   int k;
-  int kp1;       // N of the projection GEMM, K extent of the reconstruction: ceil16(k + 2) <= 64
+  int kp1;       // N of the projection GEMM, K extent of the reconstruction: ceil16(k + 2) <= 128
+  int katoms;    // 64-wide K atoms of the P and coefficient operands: ceil(kp1 / 64)
+  int rows_c;    // rows of one K atom of the packed coefficients
   int n_chunks;  // ceil(m / 64)
   int n_ct;      // ceil(2m / 64)
   int n_tiles;   // ceil(n / 128)
@@ -126,11 +128,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const bool x3 = p.x3 != 0;
   const int S = p.stages;
-  // layout: ring [S] | P operand (hi, lo) | coefficient ring [2] (hi[, lo]) | staging [4 warps] | barriers
+  // layout: ring [S] | P operand (hi, lo; katoms K atoms each) | coefficient ring [2] (hi[, lo]; katoms
+  // atoms each) | staging [4 warps] | barriers
+  const int na = p.katoms;
+  const uint32_t pop_plane = na * kPopAtom, c_plane = na * kCAtom;
+  const uint32_t d1s = 64 * na;  // TMEM columns per projection accumulator
   uint8_t* ring = smem;
   uint8_t* pop = ring + S * p.stage_bytes;
-  const uint32_t c_stage = x3 ? 2 * kCHalf : kCHalf;
-  uint8_t* cring = pop + 2 * kPopHalf;
+  const uint32_t c_stage = (x3 ? 2 : 1) * c_plane;
+  uint8_t* cring = pop + 2 * pop_plane;
   uint8_t* stg = cring + 2 * c_stage;
   const uint32_t stg_warp = kRe ? 2 * kStg : kStg;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 4 * stg_warp);
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int d = lt & 1;
         if (!tc::mbar_wait(&d1empty[d], ((lt >> 1) & 1) ^ 1)) { fail_s = 1; break; }
         tc::tc_fence_after();
-        const uint32_t dacc = tbase + d * 64;
+        const uint32_t dacc = tbase + d * d1s;
         bool ok = true;
         for (int c = 0; c < p.n_chunks; ++c, ++it) {
           const int s = it % S;
@@ -247,8 +253,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!tc::mbar_wait(&cempty[s], ((it >> 1) & 1) ^ 1)) { fail_s = 1; break; }
           uint8_t* cs = cring + s * c_stage;
           tc::mbar_arrive_expect_tx(&cfull[s], c_stage);
-          tc::tma_load_2d(cs, &tm_chi, &cfull[s], 0, ct * kNT);
-          if (x3) tc::tma_load_2d(cs + kCHalf, &tm_clo, &cfull[s], 0, ct * kNT);
+          for (int at = 0; at < na; ++at) {
+            tc::tma_load_2d(cs + at * kCAtom, &tm_chi, &cfull[s], 0, at * p.rows_c + ct * kNT);
+            if (x3) tc::tma_load_2d(cs + c_plane + at * kCAtom, &tm_clo, &cfull[s], 0, at * p.rows_c + ct * kNT);
+          }
         }
       }
     }
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ reconstruction MMAs
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, kNT);
-      const uint32_t p_hi = tc::smem_u32(pop), p_lo = p_hi + kPopHalf;
+      const uint32_t p_hi = tc::smem_u32(pop), p_lo = p_hi + pop_plane;
       uint32_t it = 0, lt = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles && !fail_s; tile += gridDim.x, ++lt) {
         if (!tc::mbar_wait(popfull, lt & 1)) { fail_s = 1; break; }
@@ -268,14 +276,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!tc::mbar_wait(&d2empty[b], ((it / kD2) & 1) ^ 1)) { ok = false; break; }
           if (!tc::mbar_wait(&cfull[s], (it >> 1) & 1)) { ok = false; break; }
           tc::tc_fence_after();
-          const uint32_t c_hi = tc::smem_u32(cring + s * c_stage), c_lo = c_hi + kCHalf;
-          const uint32_t dacc = tbase + 128 + b * kNT;
+          const uint32_t c_hi = tc::smem_u32(cring + s * c_stage), c_lo = c_hi + c_plane;
+          const uint32_t dacc = tbase + 2 * d1s + b * kNT;
           for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t o = ks * 32;
-            tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_hi + o), tc::sdesc_kmajor_sw128(c_hi + o), idesc,
+            // K step ks: atom ks / 4, 32-byte column group ks % 4 of its rows
+            const uint32_t op = (ks >> 2) * kPopAtom + (ks & 3) * 32, oc = (ks >> 2) * kCAtom + (ks & 3) * 32;
+            tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_hi + op), tc::sdesc_kmajor_sw128(c_hi + oc), idesc,
                          ks > 0 ? 1u : 0u);
-            if (x3) tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_hi + o), tc::sdesc_kmajor_sw128(c_lo + o), idesc, 1u);
-            tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_lo + o), tc::sdesc_kmajor_sw128(c_hi + o), idesc, 1u);
+            if (x3) tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_hi + op), tc::sdesc_kmajor_sw128(c_lo + oc), idesc, 1u);
+            tc::mma_bf16(dacc, tc::sdesc_kmajor_sw128(p_lo + op), tc::sdesc_kmajor_sw128(c_hi + oc), idesc, 1u);
           }
           tc::mma_commit(&cempty[s]);
           tc::mma_commit(&d2full[b]);
@@ -344,40 +353,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       failed = bar_t_any(!ok);
       if (failed) break;
       tc::tc_fence_after();
-      const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + d * 64 + 32 * h;
-      float pv[32];
+      for (int at = 0; at < na; ++at) {
+        // columns 64 at + 32 h .. + 31 of the row, into K atom `at`
+        const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + d * d1s + 64 * at + 32 * h;
+        float pv[32];
 #pragma unroll
-      for (int c16 = 0; c16 < 2; ++c16) {
-        if (2 * h + c16 < ksteps) {
-          tc::tmem_ld16(taddr + c16 * 16, pv + c16 * 16);
-        } else {
+        for (int c16 = 0; c16 < 2; ++c16) {
+          if (4 * at + 2 * h + c16 < ksteps) {
+            tc::tmem_ld16(taddr + c16 * 16, pv + c16 * 16);
+          } else {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) pv[c16 * 16 + e] = 0.f;
+            for (int e = 0; e < 16; ++e) pv[c16 * 16 + e] = 0.f;
+          }
+        }
+        uint8_t* pa = pop + at * kPopAtom;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint4 hi, lo;
+          split8(pv + 8 * q, hi, lo);
+          // columns k, k+1 carry the offset's contribution: P_hi[k] = 1 and
+          // (reduced form) P_lo[k+1] = 1, the rest 0
+          uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = 64 * at + 32 * h + 8 * q + e;
+            const uint32_t sh = (e & 1) * 16;
+            if (col >= p.k) {
+              const uint32_t one = 0x3F80u;  // bf16 1.0
+              const uint32_t hv = col == p.k ? one : 0u;
+              const uint32_t lv = (!x3 && col == p.k + 1) ? one : 0u;
+              hw[e >> 1] = (hw[e >> 1] & ~(0xFFFFu << sh)) | (hv << sh);
+              lw[e >> 1] = (lw[e >> 1] & ~(0xFFFFu << sh)) | (lv << sh);
+            }
+          }
+          *reinterpret_cast<uint4*>(pa + sw128(r, 4 * h + q)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(pa + pop_plane + sw128(r, 4 * h + q)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
       tc::tc_fence_before();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint4 hi, lo;
-        split8(pv + 8 * q, hi, lo);
-        // columns k, k+1 carry the offset's contribution: P_hi[k] = 1 and
-        // (reduced form) P_lo[k+1] = 1, the rest 0
-        uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int col = 32 * h + 8 * q + e;
-          const uint32_t sh = (e & 1) * 16;
-          if (col >= p.k) {
-            const uint32_t one = 0x3F80u;  // bf16 1.0
-            const uint32_t hv = col == p.k ? one : 0u;
-            const uint32_t lv = (!x3 && col == p.k + 1) ? one : 0u;
-            hw[e >> 1] = (hw[e >> 1] & ~(0xFFFFu << sh)) | (hv << sh);
-            lw[e >> 1] = (lw[e >> 1] & ~(0xFFFFu << sh)) | (lv << sh);
-          }
-        }
-        *reinterpret_cast<uint4*>(pop + sw128(r, 4 * h + q)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(pop + kPopHalf + sw128(r, 4 * h + q)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
       tc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) {
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = it % kD2;
         if (!warp_wait(&d2full[b], (it / kD2) & 1)) { failed = true; break; }
         tc::tc_fence_after();
-        const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + 128 + b * kNT;
+        const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + 2 * d1s + b * kNT;
         float v[64];
         tc::tmem_ld32(taddr, v);
         tc::tmem_ld32(taddr + 32, v + 32);
@@ -474,15 +487,18 @@ __global__ void pbar_kernel(const double* __restrict__ w, const double* __restri
 }
 
 // Interleaved coefficients: row 2j = log2(e) C_amp[:, j], row 2j + 1 =
-// C_ph[:, j], as bf16 hi / lo [rows_c][64]; column k holds the bias
-// b = pbar^T C of the row (hi part in both planes' hi column and its lo part
-// in the lo plane), column k + 1 the lo part of the bias in the hi plane.
+// C_ph[:, j], as bf16 hi / lo in K atoms of 64 columns, atom-major
+// [katoms][rows_c][64]; column k holds the bias b = pbar^T C of the row (hi
+// part in the hi plane, its lo part in the lo plane), column k + 1 the lo
+// part of the bias in the hi plane.
 __global__ void pack_c_kernel(const double* __restrict__ camp, const double* __restrict__ cph,
-                              const double* __restrict__ pbar, int k, int m, int rows_c,
+                              const double* __restrict__ pbar, int k, int m, int rows_c, int katoms,
                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)rows_c * kKp) return;
-  const int r = (int)(t / kKp), c = (int)(t % kKp);
+  if (t >= (int64_t)katoms * rows_c * kKp) return;
+  const int at = (int)(t / ((int64_t)rows_c * kKp));
+  const int64_t u = t - (int64_t)at * rows_c * kKp;
+  const int r = (int)(u / kKp), c = at * kKp + (int)(u % kKp);
   const int j = r >> 1;
   const double sc = (r & 1) ? 1.0 : 1.4426950408889634;
   const double* cm = (r & 1) ? cph : camp;
@@ -515,11 +531,15 @@ __global__ void chan_consts_kernel(const float* __restrict__ i_ref, const double
   cc[64] = j < m ? (float)off[j] : 0.f;
 }
 
+// Shared memory of the kernel with the deepest ring (2..4 stages, or `want`)
+// that fits; above the 227 KB limit when not even two stages do.
 size_t fused_smem(int kp1, bool x3, bool re, int want, int* stages, uint32_t* stage_bytes, uint32_t* w_bytes) {
+  const int katoms = (kp1 + kKp - 1) / kKp;
   const uint32_t wb = (uint32_t)kp1 * 128;
   uint32_t st = kIBytes + (x3 ? 2 : 1) * wb + kConstBytes;
   st = (st + 1023) & ~1023u;
-  const size_t fixed = 1024 + 2 * kPopHalf + 2 * (x3 ? 2 : 1) * kCHalf + 4 * (re ? 2 : 1) * kStg + 512;
+  const size_t fixed =
+      1024 + 2 * katoms * kPopAtom + 2 * (x3 ? 2 : 1) * katoms * kCAtom + 4 * (re ? 2 : 1) * kStg + 512;
   const size_t cap = 227 * 1024;
   int s = (want >= 2 && want <= kMaxStages) ? want : kMaxStages;
   while (s > 2 && fixed + (size_t)s * st > cap) --s;
@@ -537,9 +557,10 @@ fkk_status apply_pack(fkk_ctx* ctx, const fkk_basis* Bc, cudaStream_t st) {
   if (B->pack) return FKK_OK;
   const int m = B->m, k = B->k;
   const int kp1 = ((k + 2 + 15) / 16) * 16;
+  const int katoms = (kp1 + kKp - 1) / kKp;
   const int mp = ((m + 63) / 64) * 64;
   const int rows_c = ((2 * m + kNT - 1) / kNT) * kNT;
-  const size_t wbytes = (size_t)kp1 * mp * 2, cbytes = (size_t)rows_c * kKp * 2;
+  const size_t wbytes = (size_t)kp1 * mp * 2, cbytes = (size_t)katoms * rows_c * kKp * 2;
   const size_t bytes = 2 * wbytes + 2 * cbytes + 2 * (size_t)mp * 4 + (size_t)k * 8 + 2048;
   void* mem = nullptr;
   FKK_CUDA(ctx, cudaMalloc(&mem, bytes));
@@ -561,8 +582,8 @@ fkk_status apply_pack(fkk_ctx* ctx, const fkk_basis* Bc, cudaStream_t st) {
   FKK_COUNT_LAUNCH();
   pbar_kernel<<<k, 256, 0, st>>>(B->w, B->f, B->a_off, m, k, pbar);
   FKK_COUNT_LAUNCH();
-  pack_c_kernel<<<(unsigned)(((int64_t)rows_c * kKp + 255) / 256), 256, 0, st>>>(
-      B->c_amp, B->c_ph, pbar, k, m, rows_c, (__nv_bfloat16*)B->c_hi, (__nv_bfloat16*)B->c_lo);
+  pack_c_kernel<<<(unsigned)(((int64_t)katoms * rows_c * kKp + 255) / 256), 256, 0, st>>>(
+      B->c_amp, B->c_ph, pbar, k, m, rows_c, katoms, (__nv_bfloat16*)B->c_hi, (__nv_bfloat16*)B->c_lo);
   FKK_COUNT_LAUNCH();
   chan_consts_kernel<<<(mp + 255) / 256, 256, 0, st>>>(B->i_ref, B->a_off, m, mp, B->consts);
   cudaError_t e = cudaGetLastError();
@@ -582,27 +603,30 @@ fkk_status launch_apply_fused(fkk_ctx* ctx, const fkk_basis* B, const float* i_c
                               float* im, float* re, int64_t ld_out, cudaStream_t st, bool* handled) {
   *handled = false;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  if (ld % 4 || ld_out % 4 || !al16(i_cars) || !al16(im) || (re && !al16(re)) || B->k > 62) return FKK_OK;
+  if (ld % 4 || ld_out % 4 || !al16(i_cars) || !al16(im) || (re && !al16(re))) return FKK_OK;
   if (n > ((int64_t)1 << 31) - kTM) return FKK_OK;
   if (is_host_ptr(i_cars) || is_host_ptr(im) || (re && is_host_ptr(re))) return FKK_OK;
+  const bool x3 = B->params.precision != FKK_PREC_BF16;
+  FusedArgs a{};
+  a.kp1 = ((B->k + 2 + 15) / 16) * 16;
+  const size_t smem = fused_smem(a.kp1, x3, re != nullptr, ctx->apply_stages, &a.stages, &a.stage_bytes, &a.w_bytes);
+  // two K atoms at k > 62 fit only the single-product form; the rest takes the two-kernel path
+  if (smem > 227 * 1024) return FKK_OK;
   *handled = true;
   FKK_TRY(apply_pack(ctx, B, st));
   const int m = B->m;
-  FusedArgs a{};
   a.n = n;
   a.m = m;
   a.k = B->k;
-  a.kp1 = B->pack_kp1;
+  a.katoms = (a.kp1 + kKp - 1) / kKp;
+  a.rows_c = B->pack_rows_c;
   a.n_chunks = (m + kCh - 1) / kCh;
   a.n_ct = (2 * m + kNT - 1) / kNT;
   a.n_tiles = (int)((n + kTM - 1) / kTM);
-  a.x3 = B->params.precision == FKK_PREC_BF16 ? 0 : 1;
+  a.x3 = x3 ? 1 : 0;
   a.floor_ = B->params.ratio_floor;
   a.consts = B->consts;
   a.status = ctx->d_status;
-  const size_t smem =
-      fused_smem(a.kp1, a.x3 != 0, re != nullptr, ctx->apply_stages, &a.stages, &a.stage_bytes, &a.w_bytes);
-  if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "apply: tile does not fit shared memory");
   CUtensorMap ti, twh, twl, tch, tcl, tim, tre;
   FKK_TRY(make_tmap_2d(ctx, &ti, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<float*>(i_cars), (uint64_t)m,
                        (uint64_t)n, (uint64_t)ld * 4, 32, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
@@ -610,10 +634,11 @@ fkk_status launch_apply_fused(fkk_ctx* ctx, const fkk_basis* B, const float* i_c
                        (uint64_t)a.kp1, (uint64_t)B->pack_mp * 2, 64, (uint32_t)a.kp1, CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &twl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B->w_lo, (uint64_t)B->pack_mp,
                        (uint64_t)a.kp1, (uint64_t)B->pack_mp * 2, 64, (uint32_t)a.kp1, CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_TRY(make_tmap_2d(ctx, &tch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B->c_hi, (uint64_t)kKp,
-                       (uint64_t)B->pack_rows_c, (uint64_t)kKp * 2, 64, kNT, CU_TENSOR_MAP_SWIZZLE_128B));
-  FKK_TRY(make_tmap_2d(ctx, &tcl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B->c_lo, (uint64_t)kKp,
-                       (uint64_t)B->pack_rows_c, (uint64_t)kKp * 2, 64, kNT, CU_TENSOR_MAP_SWIZZLE_128B));
+  const uint64_t crows = (uint64_t)a.katoms * B->pack_rows_c;
+  FKK_TRY(make_tmap_2d(ctx, &tch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B->c_hi, (uint64_t)kKp, crows, (uint64_t)kKp * 2,
+                       64, kNT, CU_TENSOR_MAP_SWIZZLE_128B));
+  FKK_TRY(make_tmap_2d(ctx, &tcl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B->c_lo, (uint64_t)kKp, crows, (uint64_t)kKp * 2,
+                       64, kNT, CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &tim, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, im, (uint64_t)m, (uint64_t)n,
                        (uint64_t)ld_out * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &tre, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, re ? re : im, (uint64_t)m, (uint64_t)n,

@@ -91,8 +91,8 @@ def test_apply_bf16x3_matches_oracle(fk, ctx, cube1, k):
 
 @pytest.mark.parametrize("k", [20, 40, 80])
 def test_apply_bf16_reduced_precision(fk, ctx, cube1, k):
-    """The reduced-precision served form (k = 80 exceeds the fused kernel's
-    k <= 62 and runs fp32-accurate)."""
+    """The reduced-precision served form (at k = 80 the fused kernel runs
+    its P and coefficient operands in two K atoms)."""
     from paper_2005_07132_gb300.synth import make_cube
     b_o, basis = _oracle_basis(fk, ctx, cube1, k, precision=fk.PREC_BF16)
     new = make_cube(cube1.scene.spec, image=4, height=40, width=40, scene=cube1.scene)
@@ -134,6 +134,27 @@ def test_apply_ragged_shapes(fk, ctx, n, m, k, ld_pad, ldo_pad):
     assert ok, worst
     if ldo_pad:
         assert torch.all(im_full[:, m:] == 7.0)  # stride padding never written
+    basis.close()
+
+
+@pytest.mark.parametrize("n,m,k", [(257, 2048, 80), (129, 1600, 63), (300, 878, 72)])
+def test_apply_bf16_two_atoms_ragged(fk, ctx, n, m, k):
+    """The reduced form with k > 62 (P and coefficients in two 64-wide K
+    atoms, the bias columns in the second), with Re, ragged rows and padded
+    output rows."""
+    from paper_2005_07132_gb300.synth import CubeSpec, make_cube
+    train = make_cube(CubeSpec(24, 24, m, 6, "gauss", 50.0, seed=2000 + m))
+    b_o, basis = _oracle_basis(fk, ctx, train, k, precision=fk.PREC_BF16)
+    new = make_cube(train.scene.spec, image=2, height=1, width=n, scene=train.scene)
+    re_o, im_o = O.apply(b_o, new.i_cars)
+    im_full = torch.full((n, m + 4), 7.0, dtype=torch.float32, device="cuda")
+    re_full = torch.full((n, m + 4), 7.0, dtype=torch.float32, device="cuda")
+    im, re = fk.fkk_apply(ctx, basis, _dev(new.i_cars), im_out=im_full[:, :m], re_out=re_full[:, :m])
+    torch.cuda.synchronize()
+    e_im, e_re = rel_l2(im.cpu().numpy(), im_o), rel_l2(re.cpu().numpy(), re_o)
+    print(f"apply bf16 two atoms n={n} m={m} k={k}: rel-L2 Im {e_im:.3e}, Re {e_re:.3e}")
+    assert e_im <= 1e-3 and e_re <= 1e-3
+    assert torch.all(im_full[:, m:] == 7.0) and torch.all(re_full[:, m:] == 7.0)
     basis.close()
 
 
