@@ -12,7 +12,7 @@ on the basis, reconstruction.
 Printed (one JSON line, rank 0): value = fKK-EC spectra/s of the whole job,
 the per-stage breakdown, the roofline of the dominant stage, the same metric
 end to end (e2e: fkk_fit_basis called through the C ABI on pinned host
-buffers, two contexts on alternating streams as a stream of cubes runs; the
+buffers, three contexts on round-robin streams as a stream of cubes runs; the
 in-order and torch-copy figures beside it), the FP64 CPU oracle on a bounded
 sample of the same cube (cpu_baseline), the per-spectrum KK and the ML apply
 (fp32-accurate and reduced-precision forms, with the reduced form's measured
@@ -494,19 +494,22 @@ def run_ours(args, rank, world, local):
                                   "mode": "upload, fit, download in order on one stream"}}
         # the public call on the pinned host buffers themselves: the library
         # copies the cube in and the result out on the call's stream.  In
-        # order on one stream, then as a stream of cubes runs: two contexts
-        # (one workspace each) on two streams, step i on context i % 2, so
-        # the upload of one cube overlaps the fit and download of the other.
-        outs_h = [torch.empty_like(xh).pin_memory() for _ in range(2)]
-        ctxs = [ctx, fk.Context(local)]
-        streams = [st, torch.cuda.Stream()]
+        # order on one stream, then as a stream of cubes runs: three contexts
+        # (one workspace each) on three streams, step i on context i % 3, so
+        # that one cube uploads while another is fitted and a third downloads
+        # (two lanes left the host link idle between a lane's phases: 22.4 vs
+        # 18.2 ms per step; the link moves ~171 GB/s each way at once)
+        lanes = 3
+        outs_h = [torch.empty_like(xh).pin_memory() for _ in range(lanes)]
+        ctxs = [ctx] + [fk.Context(local) for _ in range(lanes - 1)]
+        streams = [st] + [torch.cuda.Stream() for _ in range(lanes - 1)]
 
         def host_step(i):
-            j = i % 2
+            j = i % lanes
             b, _, _ = fk.fkk_fit_basis(ctxs[j], xh, refh, prm, im_out=outs_h[j], stream=streams[j])
             return b
 
-        for i in range(2):
+        for i in range(lanes):
             bases.append(host_step(i))
         torch.cuda.synchronize()
         e0.record(st)
@@ -527,13 +530,15 @@ def run_ours(args, rank, world, local):
         for b in bases:
             b.close()
         bases.clear()
-        ctxs[1].close()
+        for c in ctxs[1:]:
+            c.close()
+        del outs_h
         torch_piped = line["e2e"]
         line["e2e"] = {"value": world * n / (host_ms / 1e3), "unit": "spectra/s",
                        "h2d_bytes_per_step": int(xh.numel() * 4 + refh.numel() * 4),
                        "d2h_bytes_per_step": int(oh.numel() * 4), "ms_per_step": host_ms,
-                       "mode": "fkk_fit_basis (C ABI) on the pinned host cube and output; two contexts on "
-                               "alternating streams, host wall clock over the steps",
+                       "mode": "fkk_fit_basis (C ABI) on the pinned host cube and output; three contexts on "
+                               "round-robin streams, host wall clock over the steps",
                        "c_abi_in_order": {"value": world * n / (host_serial_ms / 1e3), "ms_per_step": host_serial_ms,
                                           "mode": "the same call, one context, one stream"},
                        "torch_copies": torch_piped}
