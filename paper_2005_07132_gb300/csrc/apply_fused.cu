@@ -603,7 +603,10 @@ fkk_status launch_apply_fused(fkk_ctx* ctx, const fkk_basis* B, const float* i_c
                               float* im, float* re, int64_t ld_out, cudaStream_t st, bool* handled) {
   *handled = false;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  if (ld % 4 || ld_out % 4 || !al16(i_cars) || !al16(im) || (re && !al16(re))) return FKK_OK;
+  // the TMA boxes need 16-byte aligned rows; the output rows must also end
+  // on a 16-byte boundary (a store clipped at the last channel still writes
+  // the rest of its 16-byte granule, which would reach into a padded stride)
+  if (ld % 4 || ld_out % 4 || B->m % 4 || !al16(i_cars) || !al16(im) || (re && !al16(re))) return FKK_OK;
   if (n > ((int64_t)1 << 31) - kTM) return FKK_OK;
   if (is_host_ptr(i_cars) || is_host_ptr(im) || (re && is_host_ptr(re))) return FKK_OK;
   const bool x3 = B->params.precision != FKK_PREC_BF16;

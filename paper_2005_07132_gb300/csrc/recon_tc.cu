@@ -8,12 +8,16 @@
 // Operands are bf16 hi + lo (three products, fp32 accumulation), K-major
 // with the 128-byte swizzle, Kp = 64 or 128 (k zero-padded).
 //
-// Persistent CTAs of 6 warps: warp 0 issues TMA (the 128-spectrum A tile
+// Persistent CTAs of 10 warps: warp 0 issues TMA (the 128-spectrum A tile
 // once per row tile, 256-column B tiles through a 2-stage ring), warp 1
-// issues tcgen05.mma into two 256-column TMEM accumulators, warps 2..5 read
+// issues tcgen05.mma into two 256-column TMEM accumulators, warps 2..9 read
 // the accumulators (one TMEM lane per spectrum), evaluate exp / sin / cos
-// with the fast intrinsics, and store the outputs.  The epilogue of one
-// column tile overlaps the MMAs of the next.
+// with the fast intrinsics, and store the outputs: each 32-spectrum x
+// 32-channel block goes into a 128-byte-swizzled staging tile that one TMA
+// store writes (clipping rows and channels outside the arrays), or, when the
+// output rows are not 16-byte aligned, through a transpose buffer as
+// coalesced row stores.  The epilogue of one column tile overlaps the MMAs
+// of the next.
 #include "common.cuh"
 #include "fit.h"
 #include "tc.cuh"
@@ -43,12 +47,17 @@ struct ReconArgs {
 __device__ __forceinline__ uint32_t a_bytes(int kp) { return kTM * kp * 2; }
 __device__ __forceinline__ uint32_t b_bytes(int kp) { return kTN * kp * 2; }
 
+// 16-byte chunk q of row r of a 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t sw128(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
+
 // kLinear: the output is the amplitude accumulator itself plus a per-channel
-// bias (P C + 1 b^T), with no exp / sin and no Re output.
-template <bool kLinear>
+// bias (P C + 1 b^T), with no exp / sin and no Re output.  kTma: outputs
+// leave through TMA stores (tm_im, tm_re) instead of per-row stores.
+template <bool kLinear, bool kTma>
 __global__ void __launch_bounds__(kRecThreads, 1)
     recon_tc_kernel(const __grid_constant__ CUtensorMap tp_hi, const __grid_constant__ CUtensorMap tp_lo,
                     const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,
+                    const __grid_constant__ CUtensorMap tm_im, const __grid_constant__ CUtensorMap tm_re,
                     ReconArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -59,7 +68,10 @@ __global__ void __launch_bounds__(kRecThreads, 1)
   uint8_t* a_lo = a_hi + a_bytes(kp);
   uint8_t* bstage = a_lo + a_bytes(kp);
   const uint32_t bst = 2 * b_bytes(kp);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bstage + p.nst * bst);
+  // TMA output staging (1024-aligned): per epilogue warp a 32 x 32 fp32 tile for Im (and one for Re)
+  uint8_t* ostage = bstage + p.nst * bst;
+  const uint32_t ostg_warp = (p.re ? 2 : 1) * 4096;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ostage + (kTma ? kEpiWarps * ostg_warp : 0));
   uint64_t* a_full = bars;                 // A tile loaded
   uint64_t* a_empty = bars + 1;            // A tile consumed (all MMAs of the row tile done)
   uint64_t* b_full = bars + 2;             // [kMaxStages]
@@ -67,7 +79,7 @@ __global__ void __launch_bounds__(kRecThreads, 1)
   uint64_t* acc_full = b_empty + kMaxStages;   // [2] accumulator ready for the epilogue
   uint64_t* acc_empty = acc_full + 2;          // [2] accumulator drained (4 epilogue warps arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-  // per epilogue warp: a 32 x 33 transpose block for Im (and one for Re)
+  // row-store path: per epilogue warp a 32 x 33 transpose block
   float* xpose = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 256);
   __shared__ int fail_s;
 
@@ -179,7 +191,47 @@ __global__ void __launch_bounds__(kRecThreads, 1)
         // two TMEM loads (32 channel pairs) -> a 32 x 32 output block in shared
         // memory (row = spectrum) -> stores of 32 consecutive channels per row
 #pragma unroll 1
-        for (int c64 = h * (kTN / 128); c64 < (h + 1) * (kTN / 128); ++c64) {
+        for (int c64 = h * (kTN / 128); c64 < (h + 1) * (kTN / 128) && kTma; ++c64) {
+          uint8_t* so = ostage + ew * ostg_warp;
+          float im32[32], re32[32];
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float v[32];
+            tc::tmem_ld32(taddr + c64 * 64 + hh * 32, v);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const float ea = __expf(v[2 * t]);
+              if (p.re) {
+                float sn, cn;
+                __sincosf(v[2 * t + 1], &sn, &cn);
+                im32[hh * 16 + t] = ea * sn;
+                re32[hh * 16 + t] = ea * cn;
+              } else {
+                im32[hh * 16 + t] = ea * __sinf(v[2 * t + 1]);
+              }
+            }
+          }
+          if (lane == 0) tc::bulk_wait_read0();  // the previous stores have read the staging tile(s)
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            *reinterpret_cast<float4*>(so + sw128(lane, q)) =
+                make_float4(im32[4 * q], im32[4 * q + 1], im32[4 * q + 2], im32[4 * q + 3]);
+            if (p.re)
+              *reinterpret_cast<float4*>(so + 4096 + sw128(lane, q)) =
+                  make_float4(re32[4 * q], re32[4 * q + 1], re32[4 * q + 2], re32[4 * q + 3]);
+          }
+          tc::fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            const int j0 = ct * (kTN / 2) + c64 * 32;
+            tc::tma_store_2d(&tm_im, so, j0, (int)n0);
+            if (p.re) tc::tma_store_2d(&tm_re, so + 4096, j0, (int)n0);
+            tc::bulk_commit();
+          }
+        }
+#pragma unroll 1
+        for (int c64 = h * (kTN / 128); c64 < (h + 1) * (kTN / 128) && !kTma; ++c64) {
           float ex[32], cs[32];
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
@@ -220,6 +272,7 @@ __global__ void __launch_bounds__(kRecThreads, 1)
       if (fail_s) break;
     }
   }
+  if (kTma && warp >= 2 && lane == 0) tc::bulk_wait0();  // this warp's stores are complete
   __syncthreads();
   if (fail_s && threadIdx.x == 0) record_error(p.status, kErrTimeout);
   tc::tc_fence_after();
@@ -267,9 +320,10 @@ __global__ void pack_c_kernel(const double* __restrict__ camp, const double* __r
   lo[t] = l;
 }
 
-size_t recon_smem(int kp, int nst) {
+size_t recon_smem(int kp, int nst, bool tma, bool re) {
+  // TMA staging tiles, or the transpose buffers of the row-store path
   return 1024 + 2 * (size_t)kTM * kp * 2 + (size_t)nst * 2 * kTN * kp * 2 + 256 +
-         (size_t)kEpiWarps * 32 * 33 * sizeof(float);
+         (tma ? (size_t)kEpiWarps * (re ? 2 : 1) * 4096 : (size_t)kEpiWarps * 32 * 33 * sizeof(float));
 }
 
 // Packs P and C into the given scratch and launches the kernel.
@@ -298,11 +352,30 @@ fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, c
   FKK_TRY(make_tmap_2d(ctx, &tpl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, plo, kp, n_pad, rb, 64, kTM, CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &tch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, chi, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
   FKK_TRY(make_tmap_2d(ctx, &tcl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, clo, kp, rows_c, rb, 64, kTN, CU_TENSOR_MAP_SWIZZLE_128B));
+  // TMA stores need 16-byte aligned output rows that also end on a 16-byte
+  // boundary (a store clipped at the last channel still writes the rest of
+  // its 16-byte granule, which would reach into a padded row's stride); the
+  // staging must fit beside a 2-stage ring
+  const bool want_re = !linear && re;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const bool tma = !linear && ld_out % 4 == 0 && m % 4 == 0 && al16(im) && (!want_re || al16(re)) &&
+                   recon_smem(kp, 2, true, want_re) <= 227 * 1024;
   int nst = 2;
-  if (recon_smem(kp, nst) > 227 * 1024) nst = 1;
-  const size_t smem = recon_smem(kp, nst);
+  if (recon_smem(kp, nst, tma, want_re) > 227 * 1024) nst = 1;
+  const size_t smem = recon_smem(kp, nst, tma, want_re);
   if (smem > 227 * 1024) return fail(ctx, FKK_ERR_INVALID_ARG, "reconstruction tile does not fit shared memory");
-  const void* fn = linear ? (const void*)recon_tc_kernel<true> : (const void*)recon_tc_kernel<false>;
+  CUtensorMap tim, tre;
+  if (tma) {
+    FKK_TRY(make_tmap_2d(ctx, &tim, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, im, (uint64_t)m, (uint64_t)n,
+                         (uint64_t)ld_out * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B));
+    FKK_TRY(make_tmap_2d(ctx, &tre, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, want_re ? re : im, (uint64_t)m, (uint64_t)n,
+                         (uint64_t)ld_out * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B));
+  } else {
+    tim = tph;  // unused by the kernel
+    tre = tph;
+  }
+  const void* fn = linear ? (const void*)recon_tc_kernel<true, false>
+                          : (tma ? (const void*)recon_tc_kernel<false, true> : (const void*)recon_tc_kernel<false, false>);
   FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ReconArgs a{n,      m,
               kp,     (int)(n_pad / kTM),
@@ -313,9 +386,11 @@ fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, c
   const int grid = (int)std::min<int64_t>(ctx->sm_count, a.n_row_tiles);
   FKK_COUNT_LAUNCH();
   if (linear)
-    recon_tc_kernel<true><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
+    recon_tc_kernel<true, false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
+  else if (tma)
+    recon_tc_kernel<false, true><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
   else
-    recon_tc_kernel<false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, a);
+    recon_tc_kernel<false, false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
   return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
 }
 

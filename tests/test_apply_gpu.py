@@ -111,7 +111,9 @@ def test_apply_bf16_reduced_precision(fk, ctx, cube1, k):
 @pytest.mark.parametrize("n,m,k,ld_pad,ldo_pad", [
     (1, 64, 8, 0, 0),        # one spectrum, one chunk
     (127, 301, 13, 3, 5),    # ragged rows and channels; strides not multiples of 4: two-kernel path
-    (129, 301, 13, 4, 8),    # one spectrum past a tile; padded strides (fused path)
+    (129, 301, 13, 4, 8),    # one spectrum past a tile; padded strides
+    (130, 301, 13, 3, 3),    # strides multiples of 4 but M is not: the stride padding stays untouched
+    (129, 300, 13, 4, 8),    # one spectrum past a tile; padded strides (fused path)
     (1000, 878, 40, 0, 0),
     (200, 1000, 62, 0, 0),   # the largest k of the fused kernel
     (300, 1600, 64, 0, 4),

@@ -203,7 +203,7 @@ def test_basis_math(fk, ctx, cube1, pec, sec_mode):
     assert rel_l2(cp.cpu().numpy(), out[6]) <= 1e-9
 
 
-@pytest.mark.parametrize("n,k,m,ld_pad", [(1000, 80, 300, 0), (129, 13, 877, 3), (5000, 64, 512, 0), (1, 1, 8, 0)])
+@pytest.mark.parametrize("n,k,m,ld_pad", [(1000, 80, 300, 0), (129, 13, 877, 3), (131, 20, 300, 4), (5000, 64, 512, 0), (1, 1, 8, 0)])
 def test_reconstruct_shapes(fk, ctx, n, k, m, ld_pad):
     """Tensor-core reconstruction: K padded to 64 / 128, ragged rows and
     channels, row stride above M, Im and Re."""
