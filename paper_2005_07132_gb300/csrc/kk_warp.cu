@@ -1,6 +1,6 @@
 // Per-spectrum KK (Eq. KCARS with the surrogate reference of Eq. K) with the
 // length-L transform held in registers: one warp per pair of spectra for
-// L = 1,024, two warps per pair for L = 2,048 (kk_pair_kernel below).
+// L = 1,024, four warps per pair for L = 2,048 (kk_quad_kernel below).
 //
 // As in the shared-memory kernel, two real spectra share one complex FFT
 // (z = a0 + i a1; the Hilbert multiplier -i sgn(m) maps it to H{a0} + i H{a1}).
@@ -271,40 +271,50 @@ __global__ void __launch_bounds__(R == 64 ? 192 : 384) kk_warp_kernel(KKWarpArgs
 }
 
 // ---------------------------------------------------------------------------
-// Pad length 2,048 with two warps per pair of spectra (64 threads, 32 complex
-// values each): n = t + 64 n2 (thread t, register n2), k = k2 + 32 k1.
-//   1. 32-point DFT over n2 in registers; twiddle w_2048^(t k2);
-//   2. transpose through the group's shared buffer so that thread
-//      (k2 = t / 2, h = t % 2) holds the 32 values n1 = 2 j + h;
-//   3. 32-point DFT over j, then the radix-2 step of the 64-point DFT over
-//      n1 between the lane pair (h = 0, 1) with one shuffle per value:
-//      X[k2 + 32 (k1' + 32 q)] = U0[k1'] + (-1)^q w_64^k1' U1[k1'], lane h
-//      keeping q = h;
-// the inverse runs the same steps backwards.  Twiddles and the exchange use
-// the same XOR-swizzled [k2][n1] layout, conflict-free for both patterns.
-__device__ __forceinline__ int xslot(int k2, int n1) { return k2 * 64 + (n1 ^ (2 * (k2 & 7))); }
+// Pad length 2,048 with four warps per pair of spectra (128 threads, 16
+// complex values each) in three passes, n = a + 16 e + 128 f and
+// k = g + 16 h + 128 d (a, g, f, d < 16; e, h < 8):
+//   1. thread (a, e) = t holds samples t + 128 f: 16-point DFT over f,
+//      twiddle w_128^(e g);
+//   2. through shared memory to thread (a, g' = t / 16), which holds e for
+//      g = g' and g' + 8: two 8-point DFTs over e, twiddle w_2048^(a c) with
+//      c = g + 16 h;
+//   3. through shared memory to thread c = t, which holds all a: 16-point
+//      DFT over a -> X[c + 128 d];
+// then -i sgn(k) in place and the same passes backwards.  Both exchanges
+// use layouts that are conflict-free for the writer's and the reader's
+// pattern, and the twiddle w_2048^(a c) is stored in the second layout.
+// Sixteen values per thread (a two-warp form with 32 values per thread, 168
+// registers, held twelve warps per SM and took 4.15 ms on 703,026 x 1,000;
+// this one 3.20 ms) let six pairs (24 warps) share an SM.
+__device__ __forceinline__ int qidx1(int a, int e, int g) { return g * 128 + e * 16 + a; }
+__device__ __forceinline__ int qidx2(int a, int c) { return c * 16 + (a ^ (c & 15)); }
 
-__device__ __forceinline__ void group_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void qbar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
-__device__ __forceinline__ float2 cmulf(float2 a, float2 w) {
+__device__ __forceinline__ float2 qmul(float2 a, float2 w) {
   return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
-__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 w) {  // a * conj(w)
+__device__ __forceinline__ float2 qmulc(float2 a, float2 w) {  // a * conj(w)
   return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
 }
 
+constexpr int kQuadGroups = 6;
+
 template <bool kPhase>
-__global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
+__global__ void __launch_bounds__(kQuadGroups * 128) kk_quad_kernel(KKWarpArgs p) {
   constexpr int L = 2048;
   extern __shared__ float4 smem4[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int grp = wib >> 1, ngrp = blockDim.x >> 6;
-  const int t = threadIdx.x & 63;      // thread of the pair group
-  const int h = t & 1, k2r = t >> 1;   // reader role after the transpose
+  const int lane = threadIdx.x & 31;
+  const int grp = threadIdx.x >> 7, ngrp = blockDim.x >> 7;
+  const int t = threadIdx.x & 127;
+  const int ta = t & 15, tb = t >> 4;  // (a, e) in pass 1, (a, g') in pass 2, (g, h) in pass 3
   const int bar_id = 1 + grp;
-  // layout: twiddles (2,048 float2, swizzled) | 1/I_ref (mpad) | per group: xbuf (2,048 float2), stage[2] (2 mpad)
-  float2* tw = reinterpret_cast<float2*>(smem4);
-  float* inv_ref = reinterpret_cast<float*>(tw + L);
+  // layout: tw2 (2,048 float2, second exchange layout) | tw1 (128 float2) |
+  //         1/I_ref (mpad) | per group: xbuf (2,048 float2), stage[2] (2 mpad floats each)
+  float2* tw2 = reinterpret_cast<float2*>(smem4);
+  float2* tw1 = tw2 + L;
+  float* inv_ref = reinterpret_cast<float*>(tw1 + 128);
   float2* gbase = reinterpret_cast<float2*>(inv_ref + p.mpad);
   const size_t per_grp_f2 = (size_t)L + 2 * (size_t)p.mpad;
   float2* xbuf = gbase + grp * per_grp_f2;
@@ -312,11 +322,17 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
   const int M = p.m;
   const int left = (L - M) / 2;
 
-  for (int e = threadIdx.x; e < L; e += blockDim.x) {
-    const int n1 = e & 63, k2 = e >> 6;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int a = q & 15, c = q >> 4;  // every (a, c) once
     float sv, cv;
-    sincospif(-2.0f * (float)(n1 * k2) / (float)L, &sv, &cv);
-    tw[xslot(k2, n1)] = make_float2(cv, sv);
+    sincospif(-2.0f * (float)((a * c) & (L - 1)) / (float)L, &sv, &cv);
+    tw2[qidx2(a, c)] = make_float2(cv, sv);
+  }
+  for (int q = threadIdx.x; q < 128; q += blockDim.x) {
+    const int e = q >> 4, g = q & 15;
+    float sv, cv;
+    sincospif(-2.0f * (float)(e * g) / 128.0f, &sv, &cv);
+    tw1[q] = make_float2(cv, sv);
   }
   for (int j = threadIdx.x; j < M; j += blockDim.x) inv_ref[j] = 1.0f / p.i_ref[j];
   __syncthreads();
@@ -325,12 +341,14 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
   const int64_t ngroups = (int64_t)gridDim.x * ngrp;
   int64_t pr = (int64_t)blockIdx.x * ngrp + grp;
   int sbuf = 0;
-  const int myrow = wib & 1;  // each warp of the group stages one of the two rows
+  // warps 0 and 1 of the group stage rows 0 and 1 of a pair
+  const int wg = t >> 5;
   auto issue = [&](int64_t q, float* st) {
-    const int64_t row = 2 * q + myrow;
+    if (wg > 1) return;
+    const int64_t row = 2 * q + wg;
     if (row >= p.n) return;
     const float* src = p.i_cars + row * p.ld;
-    float* dst = st + myrow * p.mpad;
+    float* dst = st + wg * p.mpad;
     int j0 = 0;
     if (p.vec16) {
       const int nv = M >> 2;
@@ -350,13 +368,13 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
     if (nx < npairs) issue(nx, stage0 + (sbuf ^ 1) * 2 * p.mpad);
     cp_commit();
     cp_wait1();
-    group_bar(bar_id);  // both rows staged
+    qbar(bar_id);  // both rows staged
     const int64_t n0 = 2 * pr;
     const bool has1 = n0 + 1 < p.n;
     float* a0 = st;
     float* a1 = st + p.mpad;
-    // a / L in place (see kk_warp_kernel); each thread of the group a share
-    for (int j = t; j < M; j += 64) {
+    // a / L in place: (ln 2 / 2L) log2(max(I / I_ref, floor))
+    for (int j = t; j < M; j += 128) {
       const float r = inv_ref[j];
       const float x0 = a0[j] * r;
       clamped += !(x0 >= p.floor_);
@@ -369,69 +387,85 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
       }
       a1[j] = v1;
     }
-    group_bar(bar_id);
-    float2 x[32];
-    rf::static_for<0, 32>([&](auto q) {
-      constexpr int n2 = decltype(q)::value;
-      const int c = min(max(t + 64 * n2 - left, 0), M - 1);
-      x[n2] = make_float2(a0[c], a1[c]);
+    qbar(bar_id);
+    float2 x[16];
+    // edge-replicated, centred padding: z[n] = a[clamp(n - left)], n = t + 128 f
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int f = decltype(q)::value;
+      const int c = min(max(t + 128 * f - left, 0), M - 1);
+      x[f] = make_float2(a0[c], a1[c]);
     });
     // ---- forward ----
-    rf::fft_dif<32, -1>(x);  // x[i] = Y[t][bitrev(i)]
-    rf::static_for<0, 32>([&](auto q) {
+    rf::fft_dif<16, -1>(x);  // x[i] = Z[g = bitrev(i)]
+    rf::static_for<0, 16>([&](auto q) {
       constexpr int i = decltype(q)::value;
-      constexpr int k2 = rf::bitrev(i, 5);
-      const int u = xslot(k2, t);
-      xbuf[u] = cmulf(x[i], tw[u]);
+      constexpr int g = rf::bitrev(i, 4);
+      xbuf[qidx1(ta, tb, g)] = qmul(x[i], tw1[tb * 16 + g]);
     });
-    group_bar(bar_id);
-    rf::static_for<0, 32>([&](auto q) {
-      constexpr int j = decltype(q)::value;
-      x[j] = xbuf[xslot(k2r, 2 * j + h)];
-    });
-    rf::fft_dif<32, -1>(x);  // x[i] = U_h[k1' = bitrev(i)]
-    // radix-2 step across the lane pair, then -i sgn(k); k = k2 + 32 (k1' + 32 h)
-    rf::static_for<0, 32>([&](auto q) {
+    qbar(bar_id);
+    rf::static_for<0, 16>([&](auto q) {  // x[8 s + e] for g = tb + 8 s
       constexpr int i = decltype(q)::value;
-      constexpr int k1 = rf::bitrev(i, 5);
-      const float2 tu = rf::twiddle<-1, k1, 64>(x[i]);
-      const float2 v = h ? tu : x[i];
-      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
-      float2 X = h ? rf::csub(o, v) : rf::cadd(v, o);  // X_h[k1']
-      const bool edge = (k1 == 0) && (k2r == 0);       // DC (h = 0) or Nyquist (h = 1)
-      X = edge ? make_float2(0.f, 0.f) : (h ? make_float2(-X.y, X.x) : make_float2(X.y, -X.x));
-      x[i] = X;
+      x[i] = xbuf[qidx1(ta, i & 7, tb + 8 * (i >> 3))];
     });
-    // ---- inverse: the radix-2 step back, U'_h = (X0 + (-1)^h X1) w_64^(-h k1')
-    rf::static_for<0, 32>([&](auto q) {
+    rf::fft_dif<8, -1, 0>(x);
+    rf::fft_dif<8, -1, 8>(x);  // x[8 s + i'] = Y[c = tb + 8 s + 16 bitrev3(i')]
+    qbar(bar_id);              // every thread has read the first exchange
+    rf::static_for<0, 16>([&](auto q) {
       constexpr int i = decltype(q)::value;
-      constexpr int k1 = rf::bitrev(i, 5);
-      const float2 X = x[i];
-      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, X.x, 1), __shfl_xor_sync(0xffffffffu, X.y, 1));
-      const float2 v = h ? rf::csub(o, X) : rf::cadd(X, o);
-      x[i] = h ? rf::twiddle<+1, k1, 64>(v) : v;
+      const int c = tb + 8 * (i >> 3) + 16 * rf::bitrev(i & 7, 3);
+      const int u = qidx2(ta, c);
+      xbuf[u] = qmul(x[i], tw2[u]);
     });
-    rf::fft_dit<32, +1>(x);  // x[j]: n1 = 2 j + h
-    group_bar(bar_id);       // every thread has read its transposed values
-    rf::static_for<0, 32>([&](auto q) {
-      constexpr int j = decltype(q)::value;
-      const int u = xslot(k2r, 2 * j + h);
-      xbuf[u] = cmulf_conj(x[j], tw[u]);
+    qbar(bar_id);
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int a = decltype(q)::value;
+      x[a] = xbuf[qidx2(a, t)];
     });
-    group_bar(bar_id);
-    rf::static_for<0, 32>([&](auto q) {
-      constexpr int k2 = decltype(q)::value;
-      x[k2] = xbuf[xslot(k2, t)];
+    rf::fft_dif<16, -1>(x);  // x[i] = X[t + 128 d], d = bitrev(i)
+    // -i sgn(k), k = t + 128 d: d < 8 below L/2; DC (t = 0, d = 0) and Nyquist (t = 0, d = 8) vanish
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      constexpr int d = rf::bitrev(i, 4);
+      const float2 v = x[i];
+      float2 r = d < 8 ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+      if (d == 0 || d == 8) r = t == 0 ? make_float2(0.f, 0.f) : r;
+      x[i] = r;
     });
-    rf::fft_dif<32, +1>(x);  // x[i] = h[t + 64 bitrev(i)]
+    // ---- inverse ----
+    rf::fft_dit<16, +1>(x);  // x[a], natural
+    qbar(bar_id);            // every thread has read the second exchange
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int a = decltype(q)::value;
+      const int u = qidx2(a, t);
+      xbuf[u] = qmulc(x[a], tw2[u]);
+    });
+    qbar(bar_id);
+    rf::static_for<0, 16>([&](auto q) {  // bit-reversed h for the DIT passes
+      constexpr int i = decltype(q)::value;
+      const int c = tb + 8 * (i >> 3) + 16 * rf::bitrev(i & 7, 3);
+      x[i] = xbuf[qidx2(ta, c)];
+    });
+    rf::fft_dit<8, +1, 0>(x);
+    rf::fft_dit<8, +1, 8>(x);  // x[8 s + e]
+    qbar(bar_id);
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int i = decltype(q)::value;
+      const int g = tb + 8 * (i >> 3);
+      xbuf[qidx1(ta, i & 7, g)] = qmulc(x[i], tw1[(i & 7) * 16 + g]);
+    });
+    qbar(bar_id);
+    rf::static_for<0, 16>([&](auto q) {  // bit-reversed g
+      constexpr int i = decltype(q)::value;
+      x[i] = xbuf[qidx1(ta, tb, rf::bitrev(i, 4))];
+    });
+    rf::fft_dit<16, +1>(x);  // x[f]: sample t + 128 f of H{a0} + i H{a1}
     float* im0 = p.im + n0 * p.ld_out;
     float* im1 = im0 + p.ld_out;
-    rf::static_for<0, 32>([&](auto q) {
-      constexpr int i = decltype(q)::value;
-      constexpr int n2 = rf::bitrev(i, 5);
-      const int j = t + 64 * n2 - left;
+    rf::static_for<0, 16>([&](auto q) {
+      constexpr int f = decltype(q)::value;
+      const int j = t + 128 * f - left;
       if ((unsigned)j < (unsigned)M) {
-        const float ph0 = x[i].x, ph1 = x[i].y;
+        const float ph0 = x[f].x, ph1 = x[f].y;
         if (kPhase) {
           im0[j] = ph0;
           if (has1) im1[j] = ph1;
@@ -447,7 +481,7 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
         }
       }
     });
-    group_bar(bar_id);  // staging and exchange buffers are rewritten next
+    qbar(bar_id);  // staging and exchange buffers are rewritten next
     sbuf ^= 1;
   }
   for (int o = 16; o > 0; o >>= 1) clamped += __shfl_xor_sync(0xffffffffu, clamped, o);
@@ -456,23 +490,23 @@ __global__ void __launch_bounds__(384) kk_pair_kernel(KKWarpArgs p) {
 }
 
 template <bool kPhase>
-fkk_status launch_pair(fkk_ctx* ctx, const KKWarpArgs& a, cudaStream_t st) {
-  const size_t fixed = sizeof(float2) * 2048 + sizeof(float) * (size_t)a.mpad;
+fkk_status launch_quad(fkk_ctx* ctx, const KKWarpArgs& a, cudaStream_t st) {
+  const size_t fixed = sizeof(float2) * (2048 + 128) + sizeof(float) * (size_t)a.mpad;
   const size_t pg = sizeof(float2) * (2048 + 2 * (size_t)a.mpad);
   const size_t cap = 227 * 1024;
-  int groups = 6;
+  int groups = kQuadGroups;
   while (groups > 1 && fixed + groups * pg > cap) --groups;
   const size_t smem = fixed + groups * pg;
   if (smem > cap) return fail(ctx, FKK_ERR_INVALID_ARG, "kk: %d channels need %zu B of shared memory", a.m, smem);
-  auto fn = kk_pair_kernel<kPhase>;
+  auto fn = kk_quad_kernel<kPhase>;
   FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t npairs = (a.n + 1) / 2;
   int64_t grid = (npairs + groups - 1) / groups;
   grid = std::min<int64_t>(grid, ctx->sm_count);
   if (grid < 1) grid = 1;
   FKK_COUNT_LAUNCH();
-  fn<<<(unsigned)grid, groups * 64, smem, st>>>(a);
-  return cuda_check(ctx, cudaGetLastError(), "kk_pair_kernel launch");
+  fn<<<(unsigned)grid, groups * 128, smem, st>>>(a);
+  return cuda_check(ctx, cudaGetLastError(), "kk_quad_kernel launch");
 }
 
 template <int R>
@@ -527,7 +561,7 @@ fkk_status launch_kk_warp(fkk_ctx* ctx, const float* i_cars, int64_t n, int m, i
   a.status = ctx->d_status;
   a.vec16 = ((reinterpret_cast<uintptr_t>(i_cars) & 15) == 0) && (ld % 4 == 0);
   *handled = true;
-  if (L == 2048) return phase ? launch_pair<true>(ctx, a, st) : launch_pair<false>(ctx, a, st);
+  if (L == 2048) return phase ? launch_quad<true>(ctx, a, st) : launch_quad<false>(ctx, a, st);
   return phase ? launch_r<32, true>(ctx, a, st) : launch_r<32, false>(ctx, a, st);
 }
 
