@@ -541,27 +541,64 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
   double* corr = (double*)workspace(ctx, "bm_corr", km * 8, &s);
   if (!corr) return s;
 
+  // The ridge operator N = (X^T X + lambda I)^-1 X^T needs only the
+  // sub-sampled rows X, and the Savitzky-Golay pseudo-inverse only the window:
+  // both run on the context's side stream beside the Hilbert transform of B
+  // and the ALS detrend, and the main stream waits before their first use.
+  const bool sg = bp.sec && bp.sec_mode != 1;
+  const int* nq_dev = nullptr;
+  double* lc = nullptr;
+  double* pinv = nullptr;
+  if (bp.pec) {
+    nq_dev = (const int*)workspace(ctx, "fit_nq", 64, &s);  // written by launch_gather_q
+    if (!nq_dev) return s;
+    lc = (double*)workspace(ctx, "bm_ridge_n", (size_t)k * nq_max * 8, &s);
+    if (!lc) return s;
+  }
+  if (sg) {
+    pinv = (double*)workspace(ctx, "bm_sgpinv", (size_t)(bp.sg_order + 1) * bp.sg_window * 8, &s);
+    if (!pinv) return s;
+  }
+  cudaStream_t aux = nullptr;
+  const bool side = bp.pec || sg;
+  if (side) {
+    FKK_TRY(side_stream(ctx, &aux));
+    FKK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
+    FKK_CUDA(ctx, cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
+    if (bp.pec) {
+      const size_t rsm = (size_t)(k * k + k * nq_max + k) * sizeof(dw::df);
+      FKK_CUDA(ctx, cudaFuncSetAttribute(ridge_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      FKK_COUNT_LAUNCH(); ridge_n_kernel<<<1, 256, rsm, aux>>>(x_rows, nq_dev, k, bp.ridge_rel, lc);
+    }
+    if (sg) {
+      FKK_COUNT_LAUNCH(); sg_pinv_kernel<<<1, 256, 0, aux>>>(bp.sg_window, bp.sg_order, pinv);
+    }
+    FKK_CUDA(ctx, cudaEventRecord(ctx->ev_join, aux));
+  }
+  bool joined = !side;
+  auto join = [&]() -> fkk_status {
+    if (!joined) {
+      joined = true;
+      return cuda_check(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "basis math join");
+    }
+    return FKK_OK;
+  };
+
   FKK_COUNT_LAUNCH(); b_from_v_kernel<<<k, 256, 0, st>>>(v, f, m, k, b);
   FKK_TRY(hilbert_rows(ctx, b, k, m, L, hb, nullptr, st));
   const unsigned ek = (unsigned)((km + 255) / 256);
   if (bp.pec) {
-    const int* nq_dev = (const int*)workspace(ctx, "fit_nq", 64, &s);  // written by launch_gather_q
-    if (!nq_dev) return s;
     double* phph = (double*)workspace(ctx, "bm_phph", (size_t)nq_max * m * 8, &s);
     if (!phph) return s;
     double* perr = (double*)workspace(ctx, "bm_perr", (size_t)nq_max * m * 8, &s);
     if (!perr) return s;
-    double* lc = (double*)workspace(ctx, "bm_ridge_n", (size_t)k * nq_max * 8, &s);
-    if (!lc) return s;
     FKK_COUNT_LAUNCH(); small_gemm_kernel<<<dim3(nq_max, 4), 256, k * sizeof(double), st>>>(x_rows, hb, k, m, phph, nq_dev);
     int P = 1;
     while (P < (m + 1) / 2) P *= 2;
     size_t als_smem = (size_t)P * (3 * sizeof(Blk) + sizeof(Vec2)) + (size_t)6 * P * sizeof(df);
     FKK_CUDA(ctx, cudaFuncSetAttribute(als_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)als_smem));
     FKK_COUNT_LAUNCH(); als_kernel<<<nq_max, 256, als_smem, st>>>(phph, m, P, bp.als_lambda, bp.als_p, bp.als_iters, perr, nq_dev);
-    const size_t rsm = (size_t)(k * k + k * nq_max + k) * sizeof(dw::df);
-    FKK_CUDA(ctx, cudaFuncSetAttribute(ridge_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    FKK_COUNT_LAUNCH(); ridge_n_kernel<<<1, 256, rsm, st>>>(x_rows, nq_dev, k, bp.ridge_rel, lc);
+    FKK_TRY(join());
     FKK_COUNT_LAUNCH(); ridge_apply_kernel<<<dim3((m + 127) / 128, k), 128, 0, st>>>(lc, perr, nq_dev, k, m, phit);
     FKK_CUDA(ctx, cudaGetLastError());
     FKK_TRY(hilbert_rows(ctx, phit, k, m, L, hphi, nullptr, st));
@@ -574,15 +611,14 @@ fkk_status launch_basis_math(fkk_ctx* ctx, const BasisParams& bp, const double* 
     if (bp.sec_mode == 1) {
       FKK_COUNT_LAUNCH(); mean_rows_kernel<<<k, 256, 0, st>>>(corr, m, vsec);
     } else {
-      double* pinv = (double*)workspace(ctx, "bm_sgpinv", (size_t)(bp.sg_order + 1) * bp.sg_window * 8, &s);
-      if (!pinv) return s;
-      FKK_COUNT_LAUNCH(); sg_pinv_kernel<<<1, 256, 0, st>>>(bp.sg_window, bp.sg_order, pinv);
+      FKK_TRY(join());
       FKK_COUNT_LAUNCH(); sg_apply_kernel<<<dim3(k, (m + 255) / 256), 256, 0, st>>>(corr, m, bp.sg_window, pinv, vsec);
       FKK_COUNT_LAUNCH(); sg_edges_kernel<<<k, 256, 0, st>>>(corr, m, bp.sg_window, bp.sg_order, pinv, vsec);
     }
   } else {
     FKK_CUDA(ctx, cudaMemsetAsync(vsec, 0, km * 8, st));
   }
+  FKK_TRY(join());
   FKK_COUNT_LAUNCH(); axpy3_kernel<<<ek, 256, 0, st>>>(corr, vsec, nullptr, -1.0, 0.0, (int64_t)km, out.c_amp);
   FKK_COUNT_LAUNCH(); axpy3_kernel<<<ek, 256, 0, st>>>(hb, phit, nullptr, -1.0, 0.0, (int64_t)km, out.c_ph);
   return cuda_check(ctx, cudaGetLastError(), "basis math launch");
