@@ -8,9 +8,9 @@
 // Operands are bf16 hi + lo (three products, fp32 accumulation), K-major
 // with the 128-byte swizzle, Kp = 64 or 128 (k zero-padded).
 //
-// Persistent CTAs of 10 warps: warp 0 issues TMA (the 128-spectrum A tile
-// once per row tile, 256-column B tiles through a 2-stage ring), warp 1
-// issues tcgen05.mma into two 256-column TMEM accumulators, warps 2..9 read
+// Persistent CTAs: warp 0 issues TMA (the 128-spectrum A tile once per row
+// tile, 256-column B tiles through a 2-stage ring), warp 1 issues
+// tcgen05.mma into two 256-column TMEM accumulators, 8 or 16 warps after them read
 // the accumulators (one TMEM lane per spectrum), evaluate exp / sin / cos
 // with the fast intrinsics, and store the outputs: each 32-spectrum x
 // 32-channel block goes into a 128-byte-swizzled staging tile that one TMA
@@ -27,8 +27,11 @@ namespace {
 
 constexpr int kTM = 128, kTN = 256;
 constexpr int kMaxStages = 2;
-constexpr int kRecThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int kEpiWarps = 8;
+// warp 0 TMA, warp 1 MMA, then 8 epilogue warps, or 16 for the TMA-store
+// path without Re (its staging tiles fit shared memory twice over)
+constexpr int kEpiWarpsRow = 8, kEpiWarpsTma = 16;
+template <int kEpi>
+constexpr int rec_threads() { return 64 + 32 * kEpi; }
 
 struct ReconArgs {
   int64_t n;        // spectra
@@ -52,9 +55,10 @@ __device__ __forceinline__ uint32_t sw128(int r, int q) { return (uint32_t)(r * 
 
 // kLinear: the output is the amplitude accumulator itself plus a per-channel
 // bias (P C + 1 b^T), with no exp / sin and no Re output.  kTma: outputs
-// leave through TMA stores (tm_im, tm_re) instead of per-row stores.
-template <bool kLinear, bool kTma>
-__global__ void __launch_bounds__(kRecThreads, 1)
+// leave through TMA stores (tm_im, tm_re) instead of per-row stores.  kEpi:
+// epilogue warps, four per TMEM lane quarter share a tile's columns.
+template <bool kLinear, bool kTma, int kEpiWarps>
+__global__ void __launch_bounds__(rec_threads<kEpiWarps>(), 1)
     recon_tc_kernel(const __grid_constant__ CUtensorMap tp_hi, const __grid_constant__ CUtensorMap tp_lo,
                     const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,
                     const __grid_constant__ CUtensorMap tm_im, const __grid_constant__ CUtensorMap tm_re,
@@ -191,8 +195,10 @@ __global__ void __launch_bounds__(kRecThreads, 1)
         // two TMEM loads (32 channel pairs) -> a 32 x 32 output block in shared
         // memory (row = spectrum) -> stores of 32 consecutive channels per row
 #pragma unroll 1
-        for (int c64 = h * (kTN / 128); c64 < (h + 1) * (kTN / 128) && kTma; ++c64) {
+        constexpr int kBlk = (kTN / 64) / (kEpiWarps / 4);  // 32-channel blocks per warp and tile
+        for (int c64 = h * kBlk; c64 < (h + 1) * kBlk && kTma; ++c64) {
           uint8_t* so = ostage + ew * ostg_warp;
+          const bool with_re = kEpiWarps == kEpiWarpsRow && p.re != nullptr;  // the wide form writes Im only
           float im32[32], re32[32];
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(kRecThreads, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const float ea = __expf(v[2 * t]);
-              if (p.re) {
+              if (with_re) {
                 float sn, cn;
                 __sincosf(v[2 * t + 1], &sn, &cn);
                 im32[hh * 16 + t] = ea * sn;
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(kRecThreads, 1)
           for (int q = 0; q < 8; ++q) {
             *reinterpret_cast<float4*>(so + sw128(lane, q)) =
                 make_float4(im32[4 * q], im32[4 * q + 1], im32[4 * q + 2], im32[4 * q + 3]);
-            if (p.re)
+            if (with_re)
               *reinterpret_cast<float4*>(so + 4096 + sw128(lane, q)) =
                   make_float4(re32[4 * q], re32[4 * q + 1], re32[4 * q + 2], re32[4 * q + 3]);
           }
@@ -226,12 +232,12 @@ __global__ void __launch_bounds__(kRecThreads, 1)
           if (lane == 0) {
             const int j0 = ct * (kTN / 2) + c64 * 32;
             tc::tma_store_2d(&tm_im, so, j0, (int)n0);
-            if (p.re) tc::tma_store_2d(&tm_re, so + 4096, j0, (int)n0);
+            if (with_re) tc::tma_store_2d(&tm_re, so + 4096, j0, (int)n0);
             tc::bulk_commit();
           }
         }
 #pragma unroll 1
-        for (int c64 = h * (kTN / 128); c64 < (h + 1) * (kTN / 128) && !kTma; ++c64) {
+        for (int c64 = h * kBlk; c64 < (h + 1) * kBlk && !kTma; ++c64) {
           float ex[32], cs[32];
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
@@ -322,8 +328,9 @@ __global__ void pack_c_kernel(const double* __restrict__ camp, const double* __r
 
 size_t recon_smem(int kp, int nst, bool tma, bool re) {
   // TMA staging tiles, or the transpose buffers of the row-store path
-  return 1024 + 2 * (size_t)kTM * kp * 2 + (size_t)nst * 2 * kTN * kp * 2 + 256 +
-         (tma ? (size_t)kEpiWarps * (re ? 2 : 1) * 4096 : (size_t)kEpiWarps * 32 * 33 * sizeof(float));
+  const size_t epi = tma ? (re ? (size_t)kEpiWarpsRow * 2 * 4096 : (size_t)kEpiWarpsTma * 4096)
+                         : (size_t)kEpiWarpsRow * 32 * 33 * sizeof(float);
+  return 1024 + 2 * (size_t)kTM * kp * 2 + (size_t)nst * 2 * kTN * kp * 2 + 256 + epi;
 }
 
 // Packs P and C into the given scratch and launches the kernel.
@@ -374,8 +381,11 @@ fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, c
     tim = tph;  // unused by the kernel
     tre = tph;
   }
-  const void* fn = linear ? (const void*)recon_tc_kernel<true, false>
-                          : (tma ? (const void*)recon_tc_kernel<false, true> : (const void*)recon_tc_kernel<false, false>);
+  const bool wide = tma && !want_re;  // 16 epilogue warps
+  const void* fn = linear ? (const void*)recon_tc_kernel<true, false, kEpiWarpsRow>
+                          : (tma ? (wide ? (const void*)recon_tc_kernel<false, true, kEpiWarpsTma>
+                                         : (const void*)recon_tc_kernel<false, true, kEpiWarpsRow>)
+                                 : (const void*)recon_tc_kernel<false, false, kEpiWarpsRow>);
   FKK_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ReconArgs a{n,      m,
               kp,     (int)(n_pad / kTM),
@@ -386,11 +396,17 @@ fkk_status recon_tc_run(fkk_ctx* ctx, const float* p, int64_t n, int k, int m, c
   const int grid = (int)std::min<int64_t>(ctx->sm_count, a.n_row_tiles);
   FKK_COUNT_LAUNCH();
   if (linear)
-    recon_tc_kernel<true, false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
+    recon_tc_kernel<true, false, kEpiWarpsRow>
+        <<<grid, rec_threads<kEpiWarpsRow>(), smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
+  else if (wide)
+    recon_tc_kernel<false, true, kEpiWarpsTma>
+        <<<grid, rec_threads<kEpiWarpsTma>(), smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
   else if (tma)
-    recon_tc_kernel<false, true><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
+    recon_tc_kernel<false, true, kEpiWarpsRow>
+        <<<grid, rec_threads<kEpiWarpsRow>(), smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
   else
-    recon_tc_kernel<false, false><<<grid, kRecThreads, smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
+    recon_tc_kernel<false, false, kEpiWarpsRow>
+        <<<grid, rec_threads<kEpiWarpsRow>(), smem, st>>>(tph, tpl, tch, tcl, tim, tre, a);
   return cuda_check(ctx, cudaGetLastError(), "recon_tc launch");
 }
 
