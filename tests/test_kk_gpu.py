@@ -61,7 +61,10 @@ def test_kk_img64_m512(ctx):
 
 
 @pytest.mark.parametrize("n,m,pad", [(1, 37, 0), (3, 37, 0), (1001, 878, 0), (257, 1000, 4096),
-                                      (64, 1600, 0), (5, 64, 64), (9, 2, 0), (33, 4096, 8192)])
+                                      (64, 1600, 0), (5, 64, 64), (9, 2, 0), (33, 4096, 8192),
+                                      # pad length 2,048 at both ends of its range: the widest
+                                      # edge padding (513) and none to spare (1,024)
+                                      (3, 513, 0), (2, 1024, 0), (4099, 1000, 0)])
 def test_kk_ragged_shapes(ctx, n, m, pad):
     r = np.random.default_rng(n * 7919 + m)
     i_ref = r.uniform(0.5, 2.0, m).astype(np.float32)
@@ -70,9 +73,9 @@ def test_kk_ragged_shapes(ctx, n, m, pad):
     _check(im, re, i, i_ref, pad)
 
 
-def test_kk_strided_rows_and_untouched_padding(ctx):
+@pytest.mark.parametrize("n,m", [(50, 300), (37, 1000)])
+def test_kk_strided_rows_and_untouched_padding(ctx, n, m):
     r = np.random.default_rng(11)
-    n, m = 50, 300
     i_ref = r.uniform(0.5, 2.0, m).astype(np.float32)
     i = (i_ref * np.exp(0.4 * r.standard_normal((n, m)))).astype(np.float32)
     re, im, im_view = _run(ctx, i, i_ref, ld=m + 13, ld_out=m + 5)
