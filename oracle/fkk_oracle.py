@@ -71,6 +71,7 @@ class FitParams:
     rsvd_seed: int = 0
     denoise_k: int = 0       # conventional workflow: 0 no SVD denoising of the raw spectra; > 0 keep that
                              # many singular triplets; < 0 the rank rule (at most k_max)
+    refine_steps: int = 0    # exact SVD: refinement steps on the kept basis (refine_basis)
 
 
 def pad_len(n_channels: int) -> int:
@@ -236,6 +237,31 @@ def eig_desc(G):
     sign = np.sign(V[idx, np.arange(V.shape[1])])
     sign[sign == 0] = 1.0
     return lam, V * sign
+
+
+def refine_basis(G, V, steps: int):
+    """Refinement of a computed basis V (M x k) of the k largest eigenpairs of
+    G = A^T A (Sec. 2.2 needs V and S of the SVD of A): each step is one
+    subspace iteration, Q = orth(G V) = orth(A^T (A V)), then the
+    Rayleigh-Ritz pairs of G on span(Q): the k x k matrix Q^T G Q =
+    U diag(mu) U^T gives V = Q U and the eigenvalues mu.  Exact eigenvectors
+    come back unchanged (up to rounding); the error of an approximate basis
+    shrinks about as lambda_{k+1} / lambda_k per step.  Returns (mu, V),
+    descending, each column's largest-magnitude component positive."""
+    G = np.asarray(G, F64)
+    V = np.asarray(V, F64)
+    mu = np.diag(V.T @ G @ V).copy()
+    for _ in range(steps):
+        Q, _ = np.linalg.qr(G @ V)
+        H = Q.T @ G @ Q
+        mu, U = np.linalg.eigh((H + H.T) / 2.0)
+        order = np.argsort(mu)[::-1]
+        mu, U = mu[order], U[:, order]
+        V = Q @ U
+    idx = np.argmax(np.abs(V), axis=0)
+    sign = np.sign(V[idx, np.arange(V.shape[1])])
+    sign[sign == 0] = 1.0
+    return mu, V * sign
 
 
 def rank_k(lam, n: int, m: int, k_max: int, eps: float = 0.0) -> int:
@@ -543,6 +569,9 @@ def fit(i_cars, i_ref, params: FitParams, f=None, out_rows=None, chunk: int = 65
         lam, Vall = eig_desc(G)
         k = params.k or rank_k(lam, N, M, params.k_max, params.rank_eps)
         V = Vall[:, :k]
+        if params.refine_steps:
+            lam_k, V = refine_basis(G, V, params.refine_steps)
+            lam = np.concatenate([lam_k, lam[k:]])
     else:
         raise ValueError(params.svd)
     s = singular_from_eig(lam[:k])
