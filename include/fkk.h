@@ -187,6 +187,8 @@ typedef struct {
   uint64_t rsvd_seed;        /* randomised: key of the Philox4x64-10 test matrix */
   int32_t denoise_k;    /* conventional_per_spectrum only: 0 no denoising; > 0 (<= 80) keep that many
                            singular vectors of the raw spectra; < 0 the rank rule (at most k_max) */
+  int32_t refine_steps; /* FKK_SVD_EXACT: refinement steps on the kept basis after the eigensolve, 0..4
+                           (see fkk_refine_basis); the randomised SVD refines through rsvd_power_iters */
 } fkk_fit_params;
 
 /* How fkk_fit_basis finds V_k and s:
@@ -204,6 +206,22 @@ typedef struct {
  *                      A^T A, and needs k >= 1. */
 enum { FKK_SVD_EXACT = 0, FKK_SVD_RANDOMIZED = 1 };
 
+/* Refinement of a kept basis of the eigensolve (Sec. 2.2 needs V and S of
+ * the SVD of A; this makes a computed V_k more accurate): `steps` (1..4)
+ * times, Q = orth(G V) = orth(A^T (A V)) by Cholesky QR, then the
+ * Rayleigh-Ritz pairs of G on span(Q): Q^T G Q = U diag(mu) U^T, V = Q U,
+ * lambda = mu.  g: m x m symmetric fp64, row-major (device); v: m x k fp64,
+ * row-major (device); lam_out: k (device), descending; v_out: m x k
+ * (device, may be v), each column's largest-magnitude component positive.
+ * fp64 throughout.  Exact eigenvectors come back unchanged up to rounding;
+ * the error of an approximate basis shrinks about as lambda_{k+1} /
+ * lambda_k per step.  2 <= m <= 2048, 1 <= k <= min(m, 80); otherwise
+ * FKK_ERR_INVALID_ARG.  Asynchronous on `stream`; device-side failures
+ * (a singular Q^T Q) show in fkk_sync_status.  fkk_fit_basis runs it when
+ * params.refine_steps > 0 (exact SVD). */
+fkk_status fkk_refine_basis(fkk_ctx* ctx, const double* g, int32_t m, int32_t k, const double* v, int32_t steps,
+                            double* lam_out, double* v_out, void* stream);
+
 /* The randomised SVD's test-matrix entries 0..count-1 for `seed` (as
  * described above), written as doubles to the device array out.
  * Asynchronous on `stream`. */
@@ -213,7 +231,7 @@ fkk_status fkk_philox_normals(fkk_ctx* ctx, int64_t count, uint64_t seed, double
  * als_iters 20, ridge_rel 1e-3, sec_mode SAVGOL, sg_window 0 (auto),
  * sg_order 2, ml_lambda 0, precision BF16X3, ratio_floor 1e-6, noise 0/0,
  * k_max 80, rank_eps 0 (FLT_EPSILON), svd EXACT, rsvd_oversample 10,
- * rsvd_power_iters 2, rsvd_seed 0, denoise_k 0.
+ * rsvd_power_iters 2, rsvd_seed 0, denoise_k 0, refine_steps 0.
  *
  * k = 0 selects the number of basis vectors by the rank rule of Sec. 4.1:
  * the count of singular values s_i > s_1 * max(N, M) * rank_eps (the NumPy /

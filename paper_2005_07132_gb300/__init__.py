@@ -24,6 +24,7 @@ from ._lib import (  # noqa: F401
     fkk_basis_load,
     fkk_basis_math,
     fkk_eig_topk,
+    fkk_refine_basis,
     fkk_fit_basis,
     fkk_fit_many,
     CubeJob,
@@ -43,7 +44,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "Basis", "Context", "FitParams", "FkkError", "PREC_BF16", "PREC_BF16X3", "SEC_MEAN", "SEC_SAVGOL", "SVD_EXACT", "SVD_RANDOMIZED", "fit_params", "fkk_apply",
-    "fkk_basis_from_arrays", "fkk_basis_load", "fkk_noise_scale", "Server", "fkk_basis_math", "fkk_eig_topk", "fkk_fit_basis", "fkk_fit_many", "CubeJob", "fkk_gram", "fkk_project",
+    "fkk_basis_from_arrays", "fkk_basis_load", "fkk_noise_scale", "Server", "fkk_basis_math", "fkk_eig_topk", "fkk_refine_basis", "fkk_fit_basis", "fkk_fit_many", "CubeJob", "fkk_gram", "fkk_project",
     "fkk_reconstruct", "fkk_reconstruct_noalloc", "kk_per_spectrum", "conventional_per_spectrum", "fkk_residual", "fkk_philox_normals",
     "launch_count", "lib",
 ]

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fkk_basis_from_arrays": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, C.POINTER(_P)]),
     "fkk_gram": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _P]),
     "fkk_eig_topk": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "fkk_refine_basis": (_I32, [_P, _P, _I32, _I32, _P, _I32, _P, _P, _P]),
     "fkk_project": (_I32, [_P, _P, _I64, _I32, _I64, _P, _F32, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_basis_math": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "fkk_reconstruct": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
@@ -98,6 +99,7 @@ class FitParams(C.Structure):
         ("svd", C.c_int32), ("rsvd_oversample", C.c_int32), ("rsvd_power_iters", C.c_int32),
         ("rsvd_seed", C.c_uint64),
         ("denoise_k", C.c_int32),
+        ("refine_steps", C.c_int32),
     ]
 
 
@@ -470,6 +472,25 @@ def fkk_eig_topk(ctx: Context, g, k: int, stream=None):
     st = lib().fkk_eig_topk(ctx.handle, _ptr(g), m, k, _ptr(lam), _ptr(v), _stream(stream))
     ctx.check(st, "fkk_eig_topk")
     return lam, v
+
+
+def fkk_refine_basis(ctx: Context, g, v, steps: int = 1, stream=None):
+    """Refinement of a kept basis of G's eigensolve (C: fkk_refine_basis):
+    `steps` times V <- orth(G V) and the Rayleigh-Ritz pairs of G.  g: m x m
+    float64, v: m x k float64, both contiguous on the device.  Returns
+    (lam, v_out)."""
+    import torch
+
+    _dense(g, "g")
+    _dense(v, "v")
+    m, k = v.shape
+    if g.shape != (m, m) or g.dtype != torch.float64 or v.dtype != torch.float64 or g.device != v.device:
+        raise ValueError("g must be m x m and v m x k, float64, on one device")
+    lam = torch.empty(k, dtype=torch.float64, device=v.device)
+    out = torch.empty((m, k), dtype=torch.float64, device=v.device)
+    st = lib().fkk_refine_basis(ctx.handle, _ptr(g), m, k, _ptr(v), int(steps), _ptr(lam), _ptr(out), _stream(stream))
+    ctx.check(st, "fkk_refine_basis")
+    return lam, out
 
 
 def fkk_project(ctx: Context, i_cars, i_ref, w, ratio_floor: float = 1e-6, f=None, argext: bool = True,

@@ -152,7 +152,12 @@ fkk_status check_params(fkk_ctx* ctx, const fkk_fit_params& p, int m, int64_t n)
       return fail(ctx, FKK_ERR_INVALID_ARG, "randomised SVD: k + oversample = %d must be <= 80", p.k + p.rsvd_oversample);
     if (p.rsvd_power_iters < 0 || p.rsvd_power_iters > 20)
       return fail(ctx, FKK_ERR_INVALID_ARG, "randomised SVD: power_iters %d not in 0..20", p.rsvd_power_iters);
+    if (p.refine_steps != 0)
+      return fail(ctx, FKK_ERR_INVALID_ARG, "refine_steps applies to the exact SVD (the randomised SVD refines "
+                                            "through rsvd_power_iters)");
   }
+  if (p.refine_steps < 0 || p.refine_steps > 4)
+    return fail(ctx, FKK_ERR_INVALID_ARG, "refine_steps %d not in 0..4", p.refine_steps);
   return FKK_OK;
 }
 
@@ -253,6 +258,7 @@ void fkk_fit_params_default(fkk_fit_params* p) {
   p->noise_sigma_g = 0.0;
   p->k_max = 80;
   p->rank_eps = 0.0;
+  p->refine_steps = 0;
   p->svd = FKK_SVD_EXACT;
   p->rsvd_oversample = 10;
   p->rsvd_power_iters = 2;
@@ -394,6 +400,8 @@ fkk_status fkk_fit_basis(fkk_ctx* ctx, const float* i_cars, int64_t n, int32_t m
     } else {
       if ((s = launch_eig_topk(ctx, G, m, k, B->lam, B->v, st))) return bail(s);
     }
+    if (p.refine_steps > 0 && (s = launch_refine(ctx, G, m, k, B->v, p.refine_steps, B->lam, B->v, st)))
+      return bail(s);
   }
   B->params = p;
   B->L = L;
@@ -557,7 +565,7 @@ fkk_status fkk_basis_from_arrays(fkk_ctx* ctx, int32_t m, const fkk_fit_params* 
 // basis in the layout basis_alloc defines).
 namespace {
 constexpr char kMagic[8] = {'F', 'K', 'K', 'B', 'A', 'S', 'I', 'S'};
-constexpr uint32_t kFormat = 2;  // 2: the training offset of the log ratios follows C_ph
+constexpr uint32_t kFormat = 3;  // 2: the training offset of the log ratios follows C_ph; 3: refine_steps
 struct FileHead {
   char magic[8];
   uint32_t version;

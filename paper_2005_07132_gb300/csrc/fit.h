@@ -161,6 +161,11 @@ fkk_status launch_chol_inv(fkk_ctx* ctx, const double* w, int k, double* rinv, c
 fkk_status launch_apply_rinv(fkk_ctx* ctx, const double* z, int m, int k, const double* rinv, double* v,
                              cudaStream_t st);
 fkk_status launch_sign_fix(fkk_ctx* ctx, double* v, int m, int k, cudaStream_t st);
+// Refinement of a kept basis of G's eigensolve (refine.cu): `steps` times
+// V <- orth(G V) and the Rayleigh-Ritz pairs of G on that span; lam (k) and
+// v_out (m x k, may alias v_in) receive the result.
+fkk_status launch_refine(fkk_ctx* ctx, const double* g, int m, int k, const double* v_in, int steps, double* lam,
+                         double* v_out, cudaStream_t st);
 
 // Z = A^T Q (m x l fp64) for the transformed cube and Q given as Q^T in
 // bf16 hi / lo ([tn][np], tn = 64 or 128 >= l, zero beyond l and n) with its
