@@ -1,7 +1,8 @@
 // Symmetric eigensolve of the Gram matrix for its k largest eigenpairs
 // (Sec. 2.2: V and S of the SVD of A follow from G = A^T A = V S^2 V^T):
 //   1. Householder reduction Q^T G Q = T to symmetric tridiagonal form in one
-//      persistent cooperative kernel with a single grid barrier per column;
+//      persistent cooperative kernel with one tagged all-to-all exchange per
+//      column (no grid barrier);
 //   2. the k largest eigenvalues of T by Sturm-count multisection;
 //   3. one eigenvector of T per eigenvalue from the twisted factorisation of
 //      T - lambda I (the index where the eigenvector is largest is found
