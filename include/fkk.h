@@ -493,8 +493,10 @@ fkk_status fkk_noise_scale(fkk_ctx* ctx, const float* mean_spectrum, int32_t n_c
  * tile alone, in place -- and enqueues the batch (copies in, apply, copies
  * out) on the slot's stream without waiting, so up to three batches are in
  * flight and the copies of one overlap the kernel of another.  The apply of
- * a gathered batch is replayed from a CUDA graph captured once per slot and
- * 1,024-spectrum bucket.  A request waits in the queue while every slot is
+ * a gathered batch is replayed from a CUDA graph of its slot and
+ * 1,024-spectrum bucket; fkk_serve_start captures all of them (slots x
+ * staging / 1,024 graphs) before it returns, so no request pays for a
+ * capture.  A request waits in the queue while every slot is
  * busy (admission deferred until staging frees up).  The basis must outlive
  * the server and keep its precision while the server runs. */
 typedef struct fkk_server fkk_server;

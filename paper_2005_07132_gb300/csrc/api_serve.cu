@@ -154,32 +154,41 @@ void CUDART_CB slot_done(void* arg) {
   delete d;
 }
 
+// Captures the fused apply over `bucket` rows of the slot's staging into a
+// graph; false (and graphs off for good) if capture is unavailable.
+bool capture_bucket(fkk_server* S, serve_slot& sl, int64_t bucket) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  bool ok = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  fkk_status s = FKK_OK;
+  if (ok) s = fkk_apply(S->ctx, S->basis, sl.d_in, bucket, S->m, sl.d_out, nullptr, S->m, sl.stream);
+  if (ok) ok = cudaStreamEndCapture(sl.stream, &g) == cudaSuccess && s == FKK_OK;
+  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    S->use_graphs = false;
+    return false;
+  }
+  sl.graphs.emplace(bucket, ge);
+  return true;
+}
+
+int64_t bucket_of(const fkk_server* S, int64_t rows) {
+  const int64_t b = ((rows + kBucket - 1) / kBucket) * kBucket;
+  return b > S->cap ? S->cap : b;
+}
+
 // The fused apply over `rows` rows of the slot's staging, replayed from the
-// graph of its 1,024-row bucket (captured on first use).
+// graph of its 1,024-row bucket (all captured by fkk_serve_start).
 fkk_status slot_apply(fkk_server* S, serve_slot& sl, int64_t rows) {
   const int m = S->m;
-  int64_t bucket = ((rows + kBucket - 1) / kBucket) * kBucket;
-  if (bucket > S->cap) bucket = S->cap;
+  const int64_t bucket = bucket_of(S, rows);
   if (S->use_graphs) {
     auto it = sl.graphs.find(bucket);
-    if (it == sl.graphs.end()) {
-      cudaGraph_t g = nullptr;
-      cudaGraphExec_t ge = nullptr;
-      bool ok = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      fkk_status s = FKK_OK;
-      if (ok) s = fkk_apply(S->ctx, S->basis, sl.d_in, bucket, m, sl.d_out, nullptr, m, sl.stream);
-      if (ok) ok = cudaStreamEndCapture(sl.stream, &g) == cudaSuccess && s == FKK_OK;
-      if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
-      if (g) cudaGraphDestroy(g);
-      if (!ok) {
-        // capture unavailable here: launch directly from now on
-        cudaGetLastError();
-        S->use_graphs = false;
-        return fkk_apply(S->ctx, S->basis, sl.d_in, rows, m, sl.d_out, nullptr, m, sl.stream);
-      }
-      it = sl.graphs.emplace(bucket, ge).first;
-    }
-    return cudaGraphLaunch(it->second, sl.stream) == cudaSuccess ? FKK_OK : FKK_ERR_CUDA;
+    if (it == sl.graphs.end() && capture_bucket(S, sl, bucket)) it = sl.graphs.find(bucket);
+    if (it != sl.graphs.end())
+      return cudaGraphLaunch(it->second, sl.stream) == cudaSuccess ? FKK_OK : FKK_ERR_CUDA;
   }
   return fkk_apply(S->ctx, S->basis, sl.d_in, rows, m, sl.d_out, nullptr, m, sl.stream);
 }
@@ -450,6 +459,16 @@ fkk_status fkk_serve_start(fkk_ctx* ctx, const fkk_basis* basis, const char* tun
     if (FILE* fp = std::fopen(tune_cache, "w")) {
       std::fprintf(fp, "max_batch=%lld\nstages=%d\n", (long long)S->cap, stages);
       std::fclose(fp);
+    }
+  }
+  // every bucket's graph on every slot up front, so that no request pays for
+  // a capture and an instantiation
+  for (auto& sl : S->slots) {
+    cudaStreamSynchronize(sl.stream);
+    for (int64_t b = kBucket; S->use_graphs; b += kBucket) {
+      const int64_t bucket = bucket_of(S, b);
+      if (!sl.graphs.count(bucket)) capture_bucket(S, sl, bucket);
+      if (bucket >= S->cap) break;
     }
   }
   for (auto& sl : S->slots) cudaStreamSynchronize(sl.stream);
