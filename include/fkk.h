@@ -117,6 +117,21 @@ fkk_status fkk_stage_ms(fkk_ctx* ctx, float* ms, int32_t n);
  * Copies n (<= 8) words. */
 fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n);
 
+/* Measured peak of the arithmetic the eigensolver's tridiagonal reduction
+ * (Sec. 2.2, the SVD of A through its Gram matrix) is made of: the
+ * double-word multiply-add acc * y + x (a TwoProd-based product and a
+ * TwoSum-based sum on the fp32 pipe, two flops).  One kernel on every SM at
+ * full occupancy runs 8 independent chains per thread for `iters` steps
+ * (1 .. 2^24), after a short warm-up launch, timed with CUDA events on
+ * `stream` (NULL = the legacy default stream); the call synchronises.
+ *   flops_per_s  (host, may be NULL): 2 * chains * iters / elapsed seconds
+ *   chains_out   (host, may be NULL, 8 doubles): thread 0's chain values,
+ *                chain c iterating a <- a y + x_c from a = 0 with
+ *                y = (1 - 2^-9) + 3 2^-33 and x_c = (0.1f + 2^-30) 2^-c
+ *                exactly, for a check against exact arithmetic.
+ * FKK_ERR_INVALID_ARG if both outputs are NULL or iters is out of range. */
+fkk_status fkk_dw_rate(fkk_ctx* ctx, int32_t iters, double* flops_per_s, double* chains_out, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Conventional per-spectrum KK (Eq. KCARS with the surrogate, Eq. K)   */
 /* ------------------------------------------------------------------ */

@@ -47,6 +47,7 @@ SIGNATURES = {
     "fkk_test_stall_next_eigensolve": (_I32, [_P]),
     "fkk_stage_ms": (_I32, [_P, C.POINTER(C.c_float), _I32]),
     "fkk_eig_phase_cycles": (_I32, [_P, C.POINTER(_I64), _I32]),
+    "fkk_dw_rate": (_I32, [_P, _I32, C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
     "fkk_create": (_I32, [C.POINTER(_P), _I32, _SZ]),
     "fkk_destroy": (_I32, [_P]),
     "fkk_last_error": (C.c_char_p, [_P]),
@@ -231,6 +232,14 @@ class Context:
         arr = (_I64 * 8)()
         self.check(lib().fkk_eig_phase_cycles(self._h, arr, 8), "fkk_eig_phase_cycles")
         return list(arr)[:5]
+
+    def dw_rate(self, iters=4096):
+        """(double-word flop/s, [8 chain values]) of fkk_dw_rate: the measured
+        rate of the reduction's double-word multiply-add on all SMs."""
+        rate = C.c_double()
+        chains = (C.c_double * 8)()
+        self.check(lib().fkk_dw_rate(self._h, int(iters), C.byref(rate), chains, None), "fkk_dw_rate")
+        return rate.value, list(chains)
 
     def close(self):
         if self._h:
