@@ -52,6 +52,7 @@ def test_create_rejects_bad_arguments():
     assert L.fkk_create(C.byref(h), -1, 0) == -1
     assert L.fkk_destroy(None) == 0
     assert L.kk_per_spectrum(None, None, 1, 1, 1, None, 0, 1e-6, None, None, 1, None) == -1
+    assert L.fkk_dw_rate(None, 100, None, None, None) == -1
 
 
 def _header_struct_fields(name):
