@@ -122,8 +122,9 @@ fkk_status fkk_eig_phase_cycles(fkk_ctx* ctx, int64_t* cycles, int32_t n);
  * double-word multiply-add acc * y + x (a TwoProd-based product and a
  * TwoSum-based sum on the fp32 pipe, two flops).  One kernel on every SM at
  * full occupancy runs 8 independent chains per thread for `iters` steps
- * (1 .. 2^24), after a short warm-up launch, timed with CUDA events on
- * `stream` (NULL = the legacy default stream); the call synchronises.
+ * (1 .. 2^20; about 1 ms per 1,000 steps), after a short warm-up launch,
+ * timed with CUDA events on `stream` (NULL = the legacy default stream);
+ * the call synchronises.
  *   flops_per_s  (host, may be NULL): 2 * chains * iters / elapsed seconds
  *   chains_out   (host, may be NULL, 8 doubles): thread 0's chain values,
  *                chain c iterating a <- a y + x_c from a = 0 with

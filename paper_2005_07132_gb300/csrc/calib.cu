@@ -49,7 +49,7 @@ extern "C" fkk_status fkk_dw_rate(fkk_ctx* ctx, int32_t iters, double* flops_per
                                   void* stream) {
   if (!ctx) return FKK_ERR_INVALID_ARG;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  if (iters < 1 || iters > (1 << 24) || (!flops_per_s && !chains_out))
+  if (iters < 1 || iters > (1 << 20) || (!flops_per_s && !chains_out))
     return fail(ctx, FKK_ERR_INVALID_ARG, "fkk_dw_rate: bad arguments");
   FKK_TRY(bind(ctx));
   const cudaStream_t st = as_stream(stream);
