@@ -86,6 +86,7 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v));
 }
 constexpr int kMaxPer = 4;  // vector entries per vector thread: m <= kMaxPer * threads
+constexpr int kRedA = 48;   // partials of p.v in red[48..64); the three sums of phase B use red[0..48)
 
 // Loads the words at p[i], i = i0 + r * stride (r < kMaxPer, lo <= i < m),
 // all in flight at once, and re-polls those not yet carrying `tag` until
@@ -124,11 +125,15 @@ __device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i
   }
 }
 
-// Sum of one double-word per vector warp (red[0..kVecWarps)), in warp 0.
+// Sum of one double-word per vector warp (red[0..kVecWarps)), formed by any
+// warp: each group of kVecWarps lanes runs the same butterfly over the same
+// partials (and dw::add is commutative bit for bit), so every lane of every
+// warp gets the same value.
 template <int kVecWarps>
 __device__ __forceinline__ df sum_vec_partials(const df* red) {
+  static_assert((kVecWarps & (kVecWarps - 1)) == 0 && kVecWarps <= 32, "power-of-two warp count");
   const int lane = threadIdx.x & 31;
-  df t = lane < kVecWarps ? red[lane] : dw::make(0.f);
+  df t = red[lane & (kVecWarps - 1)];
 #pragma unroll
   for (int o = kVecWarps / 2; o > 0; o >>= 1) t = dw::add(t, dw::shfl_xor(t, o));
   return t;
@@ -160,6 +165,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
   constexpr int kTrWarps = kTrThreads / 32;
   constexpr int kVecWarps = kTrWarps;  // warps that run the length-m vector phases
   constexpr int kVecThreads = kVecWarps * 32;
+  static_assert(3 * kVecWarps <= kRedA && kRedA + kVecWarps <= 64, "partial slots overlap");
   extern __shared__ df smd[];
   const int m = a.m, nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -336,23 +342,17 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         }
       }
       dot = dw::warp_sum(dot);
-      if (lane == 0) red[warp] = dot;
+      if (lane == 0) red[kRedA + warp] = dot;
     }
     if (!__syncthreads_and(ok)) return;
-    if (warp == 0) {
-      const df t = sum_vec_partials<kVecWarps>(red);
-      if (lane == 0) {
-        const df halfk = dw::mul(dw::mul(tau_cur, t), 0.5f);
-        sc[4] = halfk;
-        sc[5] = dw::sub(w[j + 1], halfk);  // w_{j+1} = p_{j+1} - halfk v_{j+1}, v_{j+1} = 1
-      }
-    }
-    __syncthreads();
+    // every warp sums the partials itself (the same butterfly, so the same
+    // value in every warp) instead of one warp and a second barrier
+    const df halfk = dw::mul(dw::mul(tau_cur, sum_vec_partials<kVecWarps>(red + kRedA)), 0.5f);
+    const df wj1 = dw::sub(w[j + 1], halfk);  // w_{j+1} = p_{j+1} - halfk v_{j+1}, v_{j+1} = 1
     mark(1);
     // B. w = p - halfk v; pivot column x = c - v w_{j+1} - w after this
     //    step's update, kept raw; the next reflector from x, with
     //    alpha = v.v' and beta = w.v' (v' = e_{j+2} + scal x below row j+2)
-    const df halfk = sc[4], wj1 = sc[5];
     df sig = dw::make(0.f), vx = dw::make(0.f), wx = dw::make(0.f);
     if (vecw) {
 #pragma unroll
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         if (i < m && i >= j + 1) {
           const df vi = v[i];
           const df wi = dw::fnma(halfk, vi, w[i]);
-          w[i] = wi;
+          if (i != j + 1) w[i] = wi;  // every warp read w[j+1] above; no one reads it after
           const df x = dw::sub(dw::fnma(vi, wj1, cbr[r]), wi);
           vn[i] = x;
           if (i == j + 1 && writer) a.d[j + 1] = x;
@@ -376,6 +376,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
       }
     }
     df tau_nxt = dw::make(0.f), scal = dw::make(0.f);
+    df s6 = dw::make(0.f), s7 = dw::make(0.f);  // v.v' and w.v' of the next reflector
     if (!last) {
       if (vecw) {
         sig = dw::warp_sum(sig);
@@ -388,23 +389,20 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         }
       }
       __syncthreads();
-      if (warp == 0) {
-        const df ts = sum_vec_partials<kVecWarps>(red);
-        const df tv = sum_vec_partials<kVecWarps>(red + kVecWarps);
-        const df tw = sum_vec_partials<kVecWarps>(red + 2 * kVecWarps);
-        if (lane == 0) {
-          reflector(vn[j + 2], ts, sc);
-          sc[6] = dw::add(v[j + 2], dw::mul(sc[2], tv));
-          sc[7] = dw::add(w[j + 2], dw::mul(sc[2], tw));
-          if (writer) {
-            a.e[j + 1] = sc[1];
-            a.tau[j + 1] = sc[0];
-          }
-        }
+      // the next reflector, formed by every warp from the same partials
+      const df ts = sum_vec_partials<kVecWarps>(red);
+      const df tv = sum_vec_partials<kVecWarps>(red + kVecWarps);
+      const df tw = sum_vec_partials<kVecWarps>(red + 2 * kVecWarps);
+      df rf[3];
+      reflector(vn[j + 2], ts, rf);
+      s6 = dw::add(v[j + 2], dw::mul(rf[2], tv));
+      s7 = dw::add(w[j + 2], dw::mul(rf[2], tw));
+      if (writer && tid == 0) {
+        a.e[j + 1] = rf[1];
+        a.tau[j + 1] = rf[0];
       }
-      __syncthreads();
-      tau_nxt = sc[0];
-      scal = sc[2];
+      tau_nxt = rf[0];
+      scal = rf[2];
     } else {
       __syncthreads();
     }
@@ -437,7 +435,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
           acc = dw::warp_sum(acc);
           if (lane == 0) {
             const df av = dw::add(col[j + 2], dw::mul(scal, acc));
-            const df pc = dw::mul(tau_nxt, dw::sub(av, dw::add(dw::mul(wc, sc[6]), dw::mul(vc, sc[7]))));
+            const df pc = dw::mul(tau_nxt, dw::sub(av, dw::add(dw::mul(wc, s6), dw::mul(vc, s7))));
             st_relaxed_u64(a.pbuf + (size_t)nxt * m + c, pack_tag(pc, tagn));
           }
         }
