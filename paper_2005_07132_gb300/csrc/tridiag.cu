@@ -44,7 +44,7 @@ using dw::df;
 // length-m vector phases and owns at most one column: m <= warps * grid.
 constexpr int kTrThreadsSmall = 256, kTrThreadsLarge = 512;
 constexpr int kWY = 32;            // reflectors per block in the back-transformation
-constexpr int kBisWarps = 4;       // multisection points per round: 32 * kBisWarps
+constexpr int kBisWarps = 4;       // warps per eigenvalue; multisection points per round: 64 * kBisWarps
 constexpr float kEpsF = 5.9604645e-08f;  // 2^-24
 
 // Reflector from alpha (first entry) and sigma = sum of squares of the rest
