@@ -115,3 +115,29 @@ def test_reconstruct_wrappers_reject_bad_arguments():
     for args in bad:
         with pytest.raises(ValueError):
             _check_reconstruct(*args)
+
+
+def test_every_entry_point_rejects_null_handles():
+    """Each entry point whose first argument is a context, basis, server or
+    array pointer returns FKK_ERR_INVALID_ARG for NULL arguments (scalars set
+    to 1) before touching a device; the few that accept NULL say so."""
+    from paper_2005_07132_gb300 import _lib
+    L = _lib.lib()
+    accepts_null = {
+        "fkk_destroy": 0,             # destroying nothing is not an error
+        "fkk_workspace_bytes": 0,     # a size, 0 without a context
+        "fkk_last_error": b"",        # a message, empty without a context
+    }
+    no_status = {"fkk_basis_free", "fkk_fit_params_default", "fkk_strerror", "fkk_version",
+                 "fkk_launch_count", "fkk_fit_params_size"}
+    scalars = (C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_float, C.c_double)
+    checked = 0
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        if not argtypes or name in no_status or argtypes[0] in scalars:
+            continue
+        args = [1 if a in scalars else None for a in argtypes]
+        got = getattr(L, name)(*args)
+        assert got == accepts_null.get(name, -1), (name, got)
+        checked += 1
+    assert checked >= 30
+
