@@ -88,28 +88,35 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 constexpr int kMaxPer = 4;  // vector entries per vector thread: m <= kMaxPer * threads
 constexpr int kRedA = 48;   // partials of p.v in red[48..64); the three sums of phase B use red[0..48)
 
-// Loads the words at p[i], i = i0 + r * stride (r < kMaxPer, lo <= i < m),
-// all in flight at once, and re-polls those not yet carrying `tag` until
-// every one does (bounded).  On timeout records FKK_ERR_TIMEOUT and raises
-// the abort flag; returns false then, or when another CTA has aborted.
-__device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i0, int stride, int lo, int m,
-                                              unsigned tag, unsigned long long (&wv)[kMaxPer], int* abort_flag,
-                                              long long* status, unsigned limit) {
-  unsigned pending = 0;
+// Loads the words at p[i] and q[i], i = i0 + r * stride (r < kMaxPer,
+// lo <= i < m) -- the p words and the pivot column of a step -- all in flight
+// at once, and re-polls those not yet carrying `tag` until every one does
+// (bounded), so a column that is already published costs no round trip of
+// its own after the p words arrive.  On timeout records FKK_ERR_TIMEOUT and
+// raises the abort flag; returns false then, or when another CTA has aborted.
+__device__ __forceinline__ bool gather_tagged(const unsigned long long* p, const unsigned long long* q, int i0,
+                                               int stride, int lo, int m, unsigned tag,
+                                               unsigned long long (&wp)[kMaxPer], unsigned long long (&wq)[kMaxPer],
+                                               int* abort_flag, long long* status, unsigned limit) {
+  unsigned pending = 0;  // bit r: wp[r]; bit kMaxPer + r: wq[r]
 #pragma unroll
   for (int r = 0; r < kMaxPer; ++r) {
     const int i = i0 + r * stride;
-    wv[r] = 0;
+    wp[r] = 0;
+    wq[r] = 0;
     if (i >= lo && i < m) {
-      wv[r] = ld_relaxed_u64(p + i);
-      pending |= 1u << r;
+      wp[r] = ld_relaxed_u64(p + i);
+      wq[r] = ld_relaxed_u64(q + i);
+      pending |= (1u << r) | (1u << (kMaxPer + r));
     }
   }
   unsigned it = 0;
   for (;;) {
 #pragma unroll
-    for (int r = 0; r < kMaxPer; ++r)
-      if (((pending >> r) & 1u) && ((unsigned)wv[r] & 3u) == tag) pending &= ~(1u << r);
+    for (int r = 0; r < kMaxPer; ++r) {
+      if (((pending >> r) & 1u) && ((unsigned)wp[r] & 3u) == tag) pending &= ~(1u << r);
+      if (((pending >> (kMaxPer + r)) & 1u) && ((unsigned)wq[r] & 3u) == tag) pending &= ~(1u << (kMaxPer + r));
+    }
     if (!pending) return true;
     if ((++it & 63u) == 0) {
       if (*(volatile int*)abort_flag) return false;
@@ -120,8 +127,10 @@ __device__ __forceinline__ bool gather_tagged(const unsigned long long* p, int i
       }
     }
 #pragma unroll
-    for (int r = 0; r < kMaxPer; ++r)
-      if ((pending >> r) & 1u) wv[r] = ld_relaxed_u64(p + i0 + r * stride);
+    for (int r = 0; r < kMaxPer; ++r) {
+      if ((pending >> r) & 1u) wp[r] = ld_relaxed_u64(p + i0 + r * stride);
+      if ((pending >> (kMaxPer + r)) & 1u) wq[r] = ld_relaxed_u64(q + i0 + r * stride);
+    }
   }
 }
 
@@ -325,8 +334,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tridiag_kernel(TridArgs a) {
         }
       }
       unsigned long long wp[kMaxPer], wcb[kMaxPer];
-      ok = gather_tagged(pb, tid, kVecThreads, j + 1, m, want, wp, a.abort_flag, a.status, a.wait_limit) &&
-           gather_tagged(cb, tid, kVecThreads, j + 1, m, want, wcb, a.abort_flag, a.status, a.wait_limit);
+      ok = gather_tagged(pb, cb, tid, kVecThreads, j + 1, m, want, wp, wcb, a.abort_flag, a.status, a.wait_limit);
 #pragma unroll
       for (int r = 0; r < kMaxPer; ++r) {
         const int i = tid + r * kVecThreads;
